@@ -1,0 +1,88 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+Each case copies oracle/oracle.c, replaces one expression with a plausible
+mistake (a dropped term, a wrong sign, a wrong index, a wrong constant, a
+wrong boundary rule), compiles the copy with the oracle's own flags, binds the
+oracle API to it, and runs the pin tests of tests/test_oracle_pins.py against
+it: at least one pin must fail. Mistakes are planted only in a temporary copy
+of the oracle, on the CPU.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import build as obuild
+
+from . import test_oracle_pins as pins
+
+MUTATIONS = {
+    "drop_dp_over_rho": ("((un * dun) + (dp * rc))", "(un * dun)"),
+    "drop_rho_du": ("a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);", "a[d][0] = (un * dW[d][0]);"),
+    "pressure_predictor_no_gamma": ("double gp = g * Wc[nv - 1];", "double gp = Wc[nv - 1];"),
+    "transverse_slope_index": ("(un * dW[d][1 + t])", "(un * dW[d][1 + d])"),
+    "predictor_sign": ("Wbar[v] = Wc[v] - s;", "Wbar[v] = Wc[v] + s;"),
+    "full_slope_at_faces": ("double hs = 0.5 * dW[d][v];", "double hs = dW[d][v];"),
+    "minmod_takes_max": ("if (a > 0.0 && b > 0.0) return (a < b) ? a : b;",
+                         "if (a > 0.0 && b > 0.0) return (a > b) ? a : b;"),
+    "hll_sign": ("(((SR * FL[v]) - (SL * FR[v]))", "(((SR * FL[v]) + (SL * FR[v]))"),
+    "hll_wave_speed": ("double a = WL[1 + d] - cL, b = WR[1 + d] - cR;",
+                       "double a = WL[1 + d] - cL, b = WR[1 + d] + cR;"),
+    "energy_flux_no_pressure": ("F[nv - 1] = (U[nv - 1] + p) * un;", "F[nv - 1] = U[nv - 1] * un;"),
+    "eos_gamma": ("W[nv - 1] = (gamma - 1.0) * (U[nv - 1] - ke);", "W[nv - 1] = gamma * (U[nv - 1] - ke);"),
+    "update_sign_y": ("acc[v] = (d == 0) ? t : (acc[v] + t);",
+                      "acc[v] = (d == 0) ? t : ((d == 1) ? (acc[v] - t) : (acc[v] + t));"),
+    "dt_max_not_sum": ("s = (d == 0) ? sd : (s + sd);", "s = (d == 0) ? sd : ((sd > s) ? sd : s);"),
+    "outflow_wraps": ("if (periodic) { gi %= n;", "if (1) { gi %= n;"),
+    "outflow_reflects_inner_cell": ("if (gi > n - 1) return n - 1;", "if (gi > n - 1) return n - 2;"),
+    "periodic_off_by_one": ("if (periodic) { gi %= n; if (gi < 0) gi += n; return gi; }",
+                            "if (periodic) { gi %= n; if (gi < 0) gi += n - 1; return gi; }"),
+}
+
+# cheapest first; a mutation is caught as soon as one of them fails
+PIN_TESTS = [
+    ("minmod", lambda o: pins.test_minmod_brute_force(o)),
+    ("hll_identical", lambda o: pins.test_hll_identical_states_is_physical_flux(o)),
+    ("hll_subsonic", lambda o: pins.test_hll_subsonic_against_hand_values(o)),
+    ("dt_closed_form", lambda o: pins.test_dt_closed_form(o)),
+    ("sod_exact", lambda o: pins.test_sod_2d_matches_exact_solution_and_rows_are_identical(o)),
+    ("free_stream", lambda o: pins.test_free_stream_is_preserved_bitwise(o, 3, (0, 0, 0))),
+    ("conservation_periodic", lambda o: pins.test_conservation_periodic(o, 1)),
+    ("conservation_bflux", lambda o: pins.test_conservation_with_boundary_fluxes(o, "sod")),
+    ("mirror_x", lambda o: pins.test_mirror_symmetry_bitwise(o, 0)),
+    ("permute_xy", lambda o: pins.test_axis_permutation_symmetry(o, 0, 1)),
+    ("outflow_at_rest", lambda o: pins.test_outflow_boundary_flux_is_physical_flux_at_rest(o)),
+    ("sod_outflow", lambda o: pins.test_sod_outflow_after_shock_exits(o)),
+    ("homologous_2d", lambda o: pins.test_homologous_expansion_matches_exact_density(o, 2)),
+    ("order_acoustic_x", lambda o: pins.test_second_order_on_smooth_acoustic_wave(o, (1, 0))),
+    ("order_acoustic_diag", lambda o: pins.test_second_order_on_smooth_acoustic_wave(o, (1, 1))),
+    ("order_advection", lambda o: pins.test_second_order_on_advected_density_wave(o)),
+]
+
+
+def _build_variant(tmp_path, name, old, new):
+    src = open(obuild.SRC).read()
+    assert src.count(old) == 1, f"mutation {name}: pattern must occur exactly once"
+    path = os.path.join(tmp_path, f"oracle_{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(tmp_path, f"liboracle_{name}.so")
+    subprocess.run(["gcc", *obuild.CFLAGS, path, "-o", so, "-lm"], check=True)
+    return so
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTATIONS[name]
+    variant = oracle.Variant(_build_variant(str(tmp_path), name, old, new))
+    variant.set_threads(min(8, os.cpu_count() or 1))
+    for pin, fn in PIN_TESTS:
+        try:
+            with np.errstate(all="ignore"):
+                fn(variant)
+        except (AssertionError, FloatingPointError, ValueError):
+            print(f"{name}: caught by {pin}")
+            return                                  # caught
+    pytest.fail(f"no pin caught mutation {name}")
