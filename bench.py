@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the block-hydro packet path; prints one JSON line.
+
+Default workload (one bench step): 3D Sedov blast on 128^3 cells as 512
+blocks of 16^3 interior cells (+2 guard layers), FP64, packets of 64 blocks,
+10 time steps: pack the initial state into the padded layout, form dt, then
+per time step guard fill + hydro task on every packet + dt reduction, and
+unpack the result. Metric: zone-updates/s (interior cells x time steps / s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sedov128|sedov256_uneven|sedov128_f32] [--no-cpu-baseline]
+
+Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
+of the workload (the path has no exchange step between replicas); `value` is
+the sum over ranks of the zone updates divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64 operations of the scheme per 3D zone update, counted from its
+# definition with each face flux, face difference and primitive conversion
+# once per zone (add, sub, mul, div, sqrt each 1): primitives 12, slopes 15,
+# predictor 64, face states 45, HLL 3 x 86, update 45, signal speed 23.
+FLOPS_PER_ZONE_3D = 462
+BYTES_PER_ZONE_3D = 80        # read U^n and write U^{n+1}: 5 vars x 8 B x 2
+FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 2032 MHz, non-FMA ops
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sedov128",
+                    choices=["sedov128", "sedov128_f32", "sedov256_uneven"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2507_09337_b300 import workloads as wl
+    if name in ("sedov128", "sedov128_f32"):
+        spec, packets = wl.sedov128_packets(64)
+        desc = "3D Sedov 128^3, 512 blocks of 16^3 + 2 guards, packets of 64, 10 steps"
+        nt = 10
+    else:
+        spec, packets = wl.sedov256_uneven_packets(0)
+        desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
+        nt = 10
+    task = "f32flux" if name.endswith("_f32") else "fp64"
+    return spec, packets, nt, task, desc
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[2:]):
+                if p.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- the oracle on the host cores
+
+def oracle_rate(spec, U0, seconds: float, max_steps: int = 50):
+    """Zone-updates/s of the oracle on the full mesh, stepping until `seconds`
+    of wall time have passed (at least one step)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    m = oracle.Mesh(**spec.oracle_kwargs())
+    U = U0.copy()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        U, _, _ = oracle.step(m, U, oracle.dt(m, U))
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= max_steps:
+            break
+    return spec.zones * n / el, threads, n, el
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2507_09337_b300 import workloads as wl
+    spec, packets, nt, task, desc = workload(args.workload)
+    U0 = wl.sedov_state(spec)
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    m = oracle.Mesh(**spec.oracle_kwargs())
+    U = U0.copy()
+    for _ in range(args.warmup):
+        U, _, _ = oracle.step(m, U, oracle.dt(m, U))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _, _ = oracle.step(m, U, oracle.dt(m, U))
+    el = time.perf_counter() - t0
+    value = spec.zones * args.steps / el
+    sample = f"{args.steps} time steps (1 per bench step) of the full {spec.zones}-zone mesh, FP64"
+    line = {
+        "impl": "reference", "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc + " (reference arm: one time step per bench step)"},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2507_09337_b300 import binding as B
+    from paper_2507_09337_b300 import build as pkgbuild
+    from paper_2507_09337_b300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pkgbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    spec, packets, nt, task_name, desc = workload(args.workload)
+    task = B.TASKS[task_name]
+    U0_host = wl.sedov_state(spec)
+    dev = torch.device("cuda", local)
+    U0_dev = torch.from_numpy(U0_host).to(dev)
+    out_dev = torch.empty_like(U0_dev)
+    mesh = B.Mesh(spec, device=f"cuda:{local}", packets=packets)
+    stream = torch.cuda.Stream(dev)
+    npk = len(mesh.packets)
+    h = mesh.handle
+    hydro_events = []
+    launches_per_step = 1 + npk + 1 + nt * (2 * npk + 1) + 1
+
+    def step(record: bool):
+        B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
+        for p in mesh.packets:
+            B.orcha_packet_run(p, B.ORCHA_TASK_SIGNAL_SPEED, stream)
+        B.orcha_dt_reduce(h, stream)
+        for _ in range(nt):
+            for p in mesh.packets:
+                B.orcha_packet_run(p, B.ORCHA_TASK_GUARD_FILL, stream)
+            for i, p in enumerate(mesh.packets):
+                if record:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    B.orcha_packet_run(p, task, stream)
+                    e1.record(stream)
+                    hydro_events.append((e0, e1, len(packets[i])))
+                else:
+                    B.orcha_packet_run(p, task, stream)
+            B.orcha_dt_reduce(h, stream)
+            B.orcha_mesh_swap(h)
+        B.orcha_mesh_store(h, out_dev.data_ptr(), False, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False)
+    stream.synchronize()
+    assert mesh.poll(stream) == 0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    assert mesh.poll(stream) == 0
+
+    zone_updates = spec.zones * nt * args.steps * world
+    value = zone_updates / (ms_max * 1e-3)
+
+    # dominant kernel: the hydro task, timed per launch on its own stream
+    durs = [(a.elapsed_time(b) * 1e-3, nblk) for a, b, nblk in hydro_events]
+    zones_per_block = spec.bs[0] * spec.bs[1] * spec.bs[2]
+    tot_s = sum(d for d, _ in durs)
+    tot_zones = sum(n for _, n in durs) * zones_per_block
+    avg_launch_s = tot_s / len(durs)
+    zones_per_launch = tot_zones / len(durs)
+    hydro_share = tot_s / (ms * 1e-3)
+    fp64_bound = task_name == "fp64"
+    if fp64_bound:
+        achieved = FLOPS_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "hydro_kernel<3,16,16,rd>", "per_launch": "one packet of 64 blocks (262144 zones)",
+                "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
+    else:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+        achieved = BYTES_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "hydro_kernel<3,16,16,float>"}
+    hbm_peak = 6489.3
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    hbm_eff = BYTES_PER_ZONE_3D * value / world / 1e9
+
+    # end to end through the public API with host buffers
+    U0_pin = torch.from_numpy(U0_host).pin_memory()
+    out_pin = torch.empty(U0_host.shape, dtype=torch.float64).pin_memory()
+    bytes_io = U0_host.nbytes
+
+    def e2e_step():
+        B.orcha_mesh_load(h, U0_pin.data_ptr(), True, stream)
+        B.orcha_mesh_advance(h, mesh.packets, task, nt, True, True, stream)
+        B.orcha_mesh_store(h, out_pin.data_ptr(), True, stream)
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+    stream.synchronize()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = zone_updates / (float(e2e_ms.item()) * 1e-3)
+    assert mesh.poll(stream) == 0
+    # the e2e run and the device-resident run computed the same state
+    assert torch.equal(out_pin, out_dev.cpu())
+
+    line = {
+        "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "task": task_name, "zones_per_step": spec.zones * nt,
+                   "l2": "inputs larger than L2 (two 164 MB state buffers + 84 MB initial state)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "hydro_share_of_step": hydro_share,
+                   "hbm": {"algorithmic_gbs": hbm_eff, "peak_gbs": hbm_peak, "frac": hbm_eff / hbm_peak,
+                           "bytes_per_zone": BYTES_PER_ZONE_3D}},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io, "api": "orcha_mesh_load(host) + orcha_mesh_advance(graph) + "
+                                                         "orcha_mesh_store(host)"},
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, n, el = oracle_rate(spec, U0_host, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} time steps of the full {spec.zones}-zone mesh in {el:.1f} s"}
+    mesh.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * orcha.h -- C ABI of the B300 block-hydro packet engine.
+ *
+ * Model (arXiv 2507.09337, "ORCHA"): a task function is a group of API
+ * calls executed on one device with no data transfer in between (section
+ * "Code Generators", definitions); the data item that feeds a device task is
+ * a data packet, one flattened structure moved as a single unit (same
+ * section); an AMR application concatenates n blocks into one packet because
+ * a single block is too small to occupy a GPU, with n chosen at run time
+ * (section "DataItem Generators"). Blocks all have the same cell count and a
+ * uniform cell size (section "Flash-X"); a halo of guard cells around each
+ * block is refreshed before the task runs, and tasks contain no
+ * communication (sections "Experiments" and "Milhoja").
+ *
+ * Here a mesh is a uniform grid of equal blocks whose state lives in device
+ * memory; a packet is a list of block ids; the task run on a packet is one
+ * step of a compressible-Euler finite-volume update on ideal gamma-law gas
+ * (MUSCL-Hancock reconstruction with minmod limiting, HLL fluxes, unsplit
+ * conservative update) plus the per-block signal speeds that give the next
+ * CFL time step.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers, all others host pointers.
+ *  - The caller owns the two state buffers and the dt scalar (any device
+ *    allocator, e.g. PyTorch); the library owns only its descriptors, small
+ *    per-block scratch arrays and staging buffers, freed by the matching
+ *    destroy call.
+ *  - Calls taking a stream are asynchronous and stream-ordered; none of them
+ *    synchronises the device except orcha_mesh_poll and the destroy calls.
+ *  - Host-detected errors are returned immediately as a negative
+ *    orcha_status, with a message in orcha_last_error() (per thread).
+ *    Errors found on the device (non-physical state, bounded wait that ran
+ *    out) are OR-ed into the mesh's device error word and reported by
+ *    orcha_mesh_poll.
+ *  - Not thread-safe per mesh: calls on one mesh must come from one thread
+ *    at a time. Different meshes are independent.
+ */
+#ifndef ORCHA_H
+#define ORCHA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ORCHA_API __attribute__((visibility("default")))
+#else
+#define ORCHA_API
+#endif
+
+typedef int32_t orcha_status;
+
+#define ORCHA_OK 0
+#define ORCHA_ERR_INVALID (-1)   /* bad argument: null pointer, size, id out of range or repeated */
+#define ORCHA_ERR_OOM (-2)       /* a device allocation failed, or an HBM budget would be exceeded */
+#define ORCHA_ERR_CUDA (-3)      /* a CUDA runtime call failed (text in orcha_last_error) */
+#define ORCHA_ERR_TIMEOUT (-4)   /* a bounded wait ran out */
+#define ORCHA_ERR_NONFINITE (-5) /* the device found rho <= 0, p <= 0 or a non-finite value */
+#define ORCHA_ERR_UNSUPPORTED (-6) /* valid request outside the built configurations */
+
+/* Bits of the device error word (orcha_mesh_poll). */
+#define ORCHA_DEVERR_NONPHYSICAL 1 /* an interior cell had rho <= 0 or p <= 0 (or NaN) */
+#define ORCHA_DEVERR_BAD_DT 2      /* the reduced signal speed was not positive and finite */
+#define ORCHA_DEVERR_TIMEOUT 4     /* a device-side bounded wait gave up */
+
+/* Tasks a packet can run (orcha_packet_run). */
+typedef enum {
+    /* Refresh the two guard layers of every packet block in the current
+     * state buffer from the neighbouring blocks' interiors; on the domain
+     * edge the boundary rule applies (outflow: zero-gradient copy of the
+     * nearest interior cell, per axis; periodic: wrap). Pure FP64 copy. */
+    ORCHA_TASK_GUARD_FILL = 0,
+    /* One MUSCL-Hancock/HLL step of every packet block in FP64: reads the
+     * current buffer (guards filled) and the device dt, writes the interiors
+     * of the other buffer and the blocks' largest signal speed
+     * sum_d (|u_d| + c) / dx_d of the new state. */
+    ORCHA_TASK_HYDRO_FP64 = 1,
+    /* As HYDRO_FP64 with reconstruction, predictor and HLL fluxes in FP32
+     * (from the FP64 state rounded to nearest); each face flux is promoted to
+     * FP64 before the conservative update, which is FP64, as are the guard
+     * fill and the dt reduction. */
+    ORCHA_TASK_HYDRO_F32FLUX = 2,
+    /* Only the blocks' largest signal speed of the current buffer (to form
+     * the first time step). */
+    ORCHA_TASK_SIGNAL_SPEED = 3
+} orcha_task;
+
+/* Mesh geometry and the caller's device buffers. */
+typedef struct orcha_mesh_desc {
+    int32_t ndim;        /* 2 or 3 */
+    int32_t nb[3];       /* blocks per axis (nb[2] = 1 in 2D) */
+    int32_t bs[3];       /* interior cells per block per axis; bs[0], bs[1] (and bs[2] in 3D)
+                            each 8, 16 or 32; bs[2] = 1 in 2D */
+    int32_t periodic[3]; /* per axis: 0 outflow (zero-gradient), 1 periodic */
+    double gamma;        /* ratio of specific heats (> 1) */
+    double cfl;          /* Courant number of the summed-direction rule
+                            dt = cfl / max_cells sum_d (|u_d| + c) / dx_d (> 0) */
+    double lo[3], hi[3]; /* domain box; dx_d = (hi_d - lo_d) / (nb_d * bs_d) */
+    double* state_dev[2];/* two caller-owned device buffers of orcha_state_elems() doubles each,
+                            layout [block][var][k][j][i] over the padded block
+                            (bs + 4 cells per active axis, i fastest), vars
+                            (rho, m_x, m_y[, m_z], E); 8-byte aligned */
+    double* dt_dev;      /* caller-owned device double: the current time step */
+} orcha_mesh_desc;
+
+typedef struct orcha_mesh orcha_mesh;     /* opaque */
+typedef struct orcha_packet orcha_packet; /* opaque */
+
+/* Number of doubles in one state buffer of this geometry (0 if invalid). */
+ORCHA_API size_t orcha_state_elems(const orcha_mesh_desc* desc);
+
+/* Validate desc and create a mesh over the caller's buffers. State buffer 0
+ * is current. Allocates the per-block signal-speed array and the error word
+ * on the current device. Errors: INVALID (geometry, null buffers), OOM, CUDA. */
+ORCHA_API orcha_status orcha_mesh_create(const orcha_mesh_desc* desc, orcha_mesh** out);
+
+/* Free the library's allocations (not the caller's buffers). Waits for the
+ * device. NULL is accepted. */
+ORCHA_API orcha_status orcha_mesh_destroy(orcha_mesh* mesh);
+
+/* Index (0 or 1) of the current state buffer. */
+ORCHA_API int32_t orcha_mesh_current(const orcha_mesh* mesh);
+
+/* Make the other state buffer current (after all packets have run a hydro
+ * task for this step). Host-side only; stream order is the caller's. */
+ORCHA_API orcha_status orcha_mesh_swap(orcha_mesh* mesh);
+
+/* Column tile of the hydro kernel: one CTA sweeps a tx x ty column tile of a
+ * block along z. Built variants: 8x8, 16x8, 16x16; tx must divide bs[0] and
+ * ty must divide bs[1]. The tile does not change any result bit (each face
+ * flux is evaluated by the same expression whatever the tiling). Errors:
+ * UNSUPPORTED (no such variant), INVALID (does not divide the block), CUDA. */
+ORCHA_API orcha_status orcha_mesh_set_tile(orcha_mesh* mesh, int32_t tx, int32_t ty);
+ORCHA_API orcha_status orcha_mesh_get_tile(const orcha_mesh* mesh, int32_t* tx, int32_t* ty);
+
+/* Pack: copy interior cells into the current state buffer. `interior` holds
+ * [block][var][k][j][i] over the interior cells only (nblocks * nvar * cells
+ * per block doubles). host_ptr != 0: `interior` is host memory (pinned for
+ * true asynchrony), staged through a library device buffer; otherwise it is
+ * a device pointer. Guards are not filled. Errors: INVALID, OOM, CUDA. */
+ORCHA_API orcha_status orcha_mesh_load(orcha_mesh* mesh, const double* interior, int32_t host_ptr, void* stream);
+
+/* Unpack: copy the interiors of the current state buffer out to `interior`
+ * (same layout and host_ptr meaning as orcha_mesh_load). */
+ORCHA_API orcha_status orcha_mesh_store(orcha_mesh* mesh, double* interior, int32_t host_ptr, void* stream);
+
+/* Create a packet over n distinct block ids of the mesh (host array, copied).
+ * Errors: INVALID (n < 1, an id outside [0, nblocks) or repeated), OOM, CUDA. */
+ORCHA_API orcha_status orcha_packet_create(orcha_mesh* mesh, const int32_t* block_ids, int32_t n, orcha_packet** out);
+
+ORCHA_API orcha_status orcha_packet_destroy(orcha_packet* packet);
+
+/* Enqueue `task` for every block of the packet on `stream` (a cudaStream_t;
+ * NULL = legacy default stream). Hydro and signal-speed tasks raise the
+ * blocks' entries of the mesh's signal-speed array; orcha_dt_reduce consumes
+ * them. Errors: INVALID, UNSUPPORTED (block size), CUDA (launch). */
+ORCHA_API orcha_status orcha_packet_run(orcha_packet* packet, orcha_task task, void* stream);
+
+/* dt_dev = cfl / (largest signal speed raised since the previous reduce, over
+ * all blocks), then clear the signal-speed array. A non-positive or
+ * non-finite maximum sets ORCHA_DEVERR_BAD_DT and leaves dt_dev unchanged. */
+ORCHA_API orcha_status orcha_dt_reduce(orcha_mesh* mesh, void* stream);
+
+/* Whole steps over a set of packets that covers the mesh:
+ *   if (init_dt) SIGNAL_SPEED on every packet, dt_reduce;
+ *   repeat nsteps: GUARD_FILL on every packet; hydro_task on every packet;
+ *                  dt_reduce; swap.
+ * use_graph != 0 captures the nsteps-step sequence in a CUDA graph the first
+ * time and replays it afterwards (the graph is cached on the mesh, keyed by
+ * the packet set, task, step count and current buffer). */
+ORCHA_API orcha_status orcha_mesh_advance(orcha_mesh* mesh, orcha_packet* const* packets, int32_t npackets,
+                                orcha_task hydro_task, int32_t nsteps, int32_t init_dt,
+                                int32_t use_graph, void* stream);
+
+/* Wait for `stream`, then read the device error word into *device_error (0 =
+ * none) and clear it. Returns NONFINITE / TIMEOUT when a bit is set. */
+ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* device_error);
+
+/* Message of the last error returned on this thread ("" if none). */
+ORCHA_API const char* orcha_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORCHA_H */

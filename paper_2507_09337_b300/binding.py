@@ -1,0 +1,284 @@
+"""Thin ctypes binding of liborcha.so (include/orcha.h), same names.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. PyTorch provides device memory (the two state buffers and dt) and
+streams. If the library is missing the import of :func:`lib` raises; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liborcha.so")
+
+ORCHA_OK = 0
+ORCHA_ERR_INVALID = -1
+ORCHA_ERR_OOM = -2
+ORCHA_ERR_CUDA = -3
+ORCHA_ERR_TIMEOUT = -4
+ORCHA_ERR_NONFINITE = -5
+ORCHA_ERR_UNSUPPORTED = -6
+
+ORCHA_DEVERR_NONPHYSICAL = 1
+ORCHA_DEVERR_BAD_DT = 2
+ORCHA_DEVERR_TIMEOUT = 4
+
+ORCHA_TASK_GUARD_FILL = 0
+ORCHA_TASK_HYDRO_FP64 = 1
+ORCHA_TASK_HYDRO_F32FLUX = 2
+ORCHA_TASK_SIGNAL_SPEED = 3
+
+TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX}
+
+
+class OrchaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"orcha status {status}: {msg}")
+        self.status = status
+
+
+class orcha_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32),
+        ("nb", ctypes.c_int32 * 3),
+        ("bs", ctypes.c_int32 * 3),
+        ("periodic", ctypes.c_int32 * 3),
+        ("gamma", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("state_dev", ctypes.c_void_p * 2),
+        ("dt_dev", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_st = ctypes.c_int32
+
+# name -> (restype, argtypes), in the order of include/orcha.h
+SIGNATURES = {
+    "orcha_state_elems": (ctypes.c_size_t, [ctypes.POINTER(orcha_mesh_desc)]),
+    "orcha_mesh_create": (_st, [ctypes.POINTER(orcha_mesh_desc), ctypes.POINTER(_vp)]),
+    "orcha_mesh_destroy": (_st, [_vp]),
+    "orcha_mesh_current": (_i32, [_vp]),
+    "orcha_mesh_swap": (_st, [_vp]),
+    "orcha_mesh_set_tile": (_st, [_vp, _i32, _i32]),
+    "orcha_mesh_get_tile": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "orcha_mesh_load": (_st, [_vp, _vp, _i32, _vp]),
+    "orcha_mesh_store": (_st, [_vp, _vp, _i32, _vp]),
+    "orcha_packet_create": (_st, [_vp, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp)]),
+    "orcha_packet_destroy": (_st, [_vp]),
+    "orcha_packet_run": (_st, [_vp, ctypes.c_int, _vp]),
+    "orcha_dt_reduce": (_st, [_vp, _vp]),
+    "orcha_mesh_advance": (_st, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _i32, _i32, _i32, _vp]),
+    "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
+    "orcha_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load liborcha.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_09337_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != ORCHA_OK:
+        raise OrchaError(status, lib().orcha_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------- same-name wrappers
+
+def orcha_state_elems(desc: orcha_mesh_desc) -> int:
+    return int(lib().orcha_state_elems(ctypes.byref(desc)))
+
+
+def orcha_mesh_create(desc: orcha_mesh_desc) -> int:
+    h = _vp()
+    _check(lib().orcha_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def orcha_mesh_destroy(mesh: int) -> None:
+    _check(lib().orcha_mesh_destroy(mesh))
+
+
+def orcha_mesh_current(mesh: int) -> int:
+    return int(lib().orcha_mesh_current(mesh))
+
+
+def orcha_mesh_swap(mesh: int) -> None:
+    _check(lib().orcha_mesh_swap(mesh))
+
+
+def orcha_mesh_set_tile(mesh: int, tx: int, ty: int) -> None:
+    _check(lib().orcha_mesh_set_tile(mesh, tx, ty))
+
+
+def orcha_mesh_get_tile(mesh: int) -> tuple:
+    tx, ty = _i32(), _i32()
+    _check(lib().orcha_mesh_get_tile(mesh, ctypes.byref(tx), ctypes.byref(ty)))
+    return tx.value, ty.value
+
+
+def orcha_mesh_load(mesh: int, interior_ptr: int, host_ptr: bool, stream=None) -> None:
+    _check(lib().orcha_mesh_load(mesh, interior_ptr, int(bool(host_ptr)), _stream_ptr(stream)))
+
+
+def orcha_mesh_store(mesh: int, interior_ptr: int, host_ptr: bool, stream=None) -> None:
+    _check(lib().orcha_mesh_store(mesh, interior_ptr, int(bool(host_ptr)), _stream_ptr(stream)))
+
+
+def orcha_packet_create(mesh: int, block_ids) -> int:
+    ids = np.ascontiguousarray(block_ids, dtype=np.int32)
+    h = _vp()
+    _check(lib().orcha_packet_create(mesh, ids.ctypes.data_as(ctypes.POINTER(_i32)), int(ids.size),
+                                     ctypes.byref(h)))
+    return h.value
+
+
+def orcha_packet_destroy(packet: int) -> None:
+    _check(lib().orcha_packet_destroy(packet))
+
+
+def orcha_packet_run(packet: int, task: int, stream=None) -> None:
+    _check(lib().orcha_packet_run(packet, int(task), _stream_ptr(stream)))
+
+
+def orcha_dt_reduce(mesh: int, stream=None) -> None:
+    _check(lib().orcha_dt_reduce(mesh, _stream_ptr(stream)))
+
+
+def orcha_mesh_advance(mesh: int, packets, task: int, nsteps: int, init_dt: bool, use_graph: bool,
+                       stream=None) -> None:
+    arr = (_vp * len(packets))(*packets)
+    _check(lib().orcha_mesh_advance(mesh, arr, len(packets), int(task), int(nsteps), int(bool(init_dt)),
+                                    int(bool(use_graph)), _stream_ptr(stream)))
+
+
+def orcha_mesh_poll(mesh: int, stream=None) -> int:
+    """Wait for the stream and return the device error word (raises if set)."""
+    err = _i32()
+    _check(lib().orcha_mesh_poll(mesh, _stream_ptr(stream), ctypes.byref(err)))
+    return err.value
+
+
+def orcha_last_error() -> str:
+    return lib().orcha_last_error().decode()
+
+
+# ---------------------------------------------------------------- torch-owned mesh
+
+class Mesh:
+    """A mesh whose two state buffers and dt are torch tensors on one CUDA
+    device; wraps the handle and its packets."""
+
+    def __init__(self, spec: wl.MeshSpec, device: str = "cuda:0", packets=None):
+        import torch
+        self.spec = spec
+        self.device = torch.device(device)
+        d = orcha_mesh_desc()
+        d.ndim = spec.ndim
+        for a in range(3):
+            d.nb[a] = spec.nb[a]
+            d.bs[a] = spec.bs[a]
+            d.periodic[a] = spec.periodic[a]
+            d.lo[a] = spec.lo[a]
+            d.hi[a] = spec.hi[a]
+        d.gamma = spec.gamma
+        d.cfl = spec.cfl
+        n = orcha_state_elems(d)
+        if n == 0:
+            raise OrchaError(ORCHA_ERR_INVALID, "invalid mesh geometry")
+        with torch.cuda.device(self.device):
+            self.state = [torch.zeros(n, dtype=torch.float64, device=self.device) for _ in range(2)]
+            self.dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+            d.state_dev[0] = self.state[0].data_ptr()
+            d.state_dev[1] = self.state[1].data_ptr()
+            d.dt_dev = self.dt.data_ptr()
+            self.desc = d
+            self.handle = orcha_mesh_create(d)
+        self.packets = []
+        if packets is None:
+            packets = [np.arange(spec.nblocks, dtype=np.int32)]
+        for ids in packets:
+            self.packets.append(orcha_packet_create(self.handle, ids))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for p in self.packets:
+                orcha_packet_destroy(p)
+            self.packets = []
+            orcha_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, U, stream=None):
+        """Copy an interior block array (numpy host array or CUDA tensor) in."""
+        import torch
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            assert U.shape == self.spec.block_shape()
+            self._host_keep = torch.from_numpy(U).pin_memory()
+            orcha_mesh_load(self.handle, self._host_keep.data_ptr(), True, stream)
+        else:
+            assert U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
+            orcha_mesh_load(self.handle, U.data_ptr(), False, stream)
+
+    def store(self, out=None, stream=None):
+        """Copy the current interiors out; returns a numpy array (host) or fills
+        `out` (a CUDA tensor of the block shape)."""
+        import torch
+        if out is not None:
+            orcha_mesh_store(self.handle, out.data_ptr(), False, stream)
+            return out
+        host = torch.empty(self.spec.block_shape(), dtype=torch.float64).pin_memory()
+        orcha_mesh_store(self.handle, host.data_ptr(), True, stream)
+        torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+        return host.numpy().copy()
+
+    def run(self, task, stream=None):
+        for p in self.packets:
+            orcha_packet_run(p, task, stream)
+
+    def advance(self, nsteps: int, task=ORCHA_TASK_HYDRO_FP64, init_dt: bool = True, use_graph: bool = False,
+                stream=None):
+        orcha_mesh_advance(self.handle, self.packets, task, nsteps, init_dt, use_graph, stream)
+
+    def poll(self, stream=None) -> int:
+        return orcha_mesh_poll(self.handle, stream)
+
+    def set_tile(self, tx: int, ty: int):
+        orcha_mesh_set_tile(self.handle, tx, ty)
+
+    def dt_value(self) -> float:
+        return float(self.dt.item())

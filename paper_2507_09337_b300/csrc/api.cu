@@ -1,0 +1,366 @@
+// api.cu -- host runtime behind include/orcha.h: mesh and packet objects,
+// argument checks, kernel launches, CUDA-graph capture of whole steps.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/orcha.h"
+#include "common.cuh"
+#include "launch.h"
+
+using orcha::MeshDev;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+orcha_status fail(orcha_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+orcha_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? ORCHA_ERR_OOM : ORCHA_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define ORCHA_CUDA(call, what)                         \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool valid_bs(int b) { return b == 8 || b == 16 || b == 32; }
+
+struct GraphEntry {
+    std::vector<const orcha_packet*> packets;
+    orcha_task task;
+    int nsteps, init_dt, start_cur;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct orcha_mesh {
+    orcha_mesh_desc desc;
+    MeshDev dev;
+    int cur = 0;
+    int nblk = 0;
+    long long ncell = 0;             // interior cells per block
+    unsigned long long* smax = nullptr;
+    int* err = nullptr;
+    double* staging = nullptr;       // device staging of interior arrays for host load/store
+    int tile_x = 8, tile_y = 8;
+    int device = 0;
+    std::vector<GraphEntry> graphs;
+};
+
+struct orcha_packet {
+    orcha_mesh* mesh;
+    int n;
+    int* ids_dev;
+};
+
+extern "C" {
+
+size_t orcha_state_elems(const orcha_mesh_desc* d) {
+    if (!d || (d->ndim != 2 && d->ndim != 3)) return 0;
+    size_t n = (size_t)(d->ndim + 2);
+    for (int a = 0; a < 3; ++a) {
+        if (d->nb[a] < 1 || d->bs[a] < 1) return 0;
+        n *= (size_t)d->nb[a] * (size_t)(a < d->ndim ? d->bs[a] + 2 * orcha::kGuard : 1);
+    }
+    return n;
+}
+
+orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
+    if (!d || !out) return fail(ORCHA_ERR_INVALID, "mesh_create: null argument");
+    *out = nullptr;
+    if (d->ndim != 2 && d->ndim != 3) return fail(ORCHA_ERR_INVALID, "mesh_create: ndim must be 2 or 3");
+    for (int a = 0; a < 3; ++a) {
+        if (d->nb[a] < 1) return fail(ORCHA_ERR_INVALID, "mesh_create: nb[%d] < 1", a);
+        if (a < d->ndim && !valid_bs(d->bs[a]))
+            return fail(ORCHA_ERR_INVALID, "mesh_create: bs[%d] = %d (must be 8, 16 or 32)", a, d->bs[a]);
+        if (a >= d->ndim && (d->bs[a] != 1 || d->nb[a] != 1))
+            return fail(ORCHA_ERR_INVALID, "mesh_create: 2D meshes need nb[2] = bs[2] = 1");
+        if (a < d->ndim && !(d->hi[a] > d->lo[a])) return fail(ORCHA_ERR_INVALID, "mesh_create: hi[%d] <= lo[%d]", a, a);
+        if (d->periodic[a] != 0 && d->periodic[a] != 1) return fail(ORCHA_ERR_INVALID, "mesh_create: periodic flag");
+    }
+    if (!(d->gamma > 1.0) || !(d->cfl > 0.0)) return fail(ORCHA_ERR_INVALID, "mesh_create: need gamma > 1, cfl > 0");
+    if (!d->state_dev[0] || !d->state_dev[1] || !d->dt_dev || d->state_dev[0] == d->state_dev[1])
+        return fail(ORCHA_ERR_INVALID, "mesh_create: two distinct state buffers and dt_dev are required");
+    if (((uintptr_t)d->state_dev[0] | (uintptr_t)d->state_dev[1] | (uintptr_t)d->dt_dev) & 7)
+        return fail(ORCHA_ERR_INVALID, "mesh_create: buffers must be 8-byte aligned");
+    const long long nblk = (long long)d->nb[0] * d->nb[1] * d->nb[2];
+    if (nblk > (1LL << 30)) return fail(ORCHA_ERR_INVALID, "mesh_create: too many blocks");
+
+    orcha_mesh* m = new orcha_mesh();
+    m->desc = *d;
+    m->nblk = (int)nblk;
+    cudaGetDevice(&m->device);
+    MeshDev& v = m->dev;
+    v.ndim = d->ndim;
+    v.nvar = d->ndim + 2;
+    for (int a = 0; a < 3; ++a) {
+        v.nb[a] = d->nb[a];
+        v.bs[a] = d->bs[a];
+        v.pad[a] = a < d->ndim ? d->bs[a] + 2 * orcha::kGuard : 1;
+        v.periodic[a] = d->periodic[a];
+        // dx_d = (hi_d - lo_d) / N_d and 1/dx_d, formed in FP64 exactly as the definition does
+        const double dx = (d->hi[a] - d->lo[a]) / (double)(d->nb[a] * d->bs[a]);
+        v.idx[a] = 1.0 / dx;
+    }
+    v.var_stride = (long long)v.pad[0] * v.pad[1] * v.pad[2];
+    v.blk_stride = v.var_stride * v.nvar;
+    v.gamma = d->gamma;
+    v.gm1 = d->gamma - 1.0;
+    v.igm1 = 1.0 / (d->gamma - 1.0);
+    v.cfl = d->cfl;
+    v.dt = d->dt_dev;
+    m->ncell = (long long)d->bs[0] * d->bs[1] * d->bs[2];
+
+    cudaError_t e = cudaMalloc(&m->smax, sizeof(unsigned long long) * nblk);
+    if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->smax, 0, sizeof(unsigned long long) * nblk);
+    if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
+    // default tile: 16 wide where the block allows it
+    m->tile_x = d->bs[0] >= 16 ? 16 : 8;
+    m->tile_y = d->bs[1] >= 16 ? 16 : 8;
+    if (e == cudaSuccess) e = orcha::configure_hydro(d->ndim, m->tile_x, m->tile_y);
+    if (e != cudaSuccess) {
+        orcha_status s = cuda_fail(e, "mesh_create");
+        orcha_mesh_destroy(m);
+        return s;
+    }
+    v.smax = m->smax;
+    v.err = m->err;
+    *out = m;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_destroy(orcha_mesh* m) {
+    if (!m) return ORCHA_OK;
+    cudaDeviceSynchronize();
+    for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);
+    cudaFree(m->smax);
+    cudaFree(m->err);
+    cudaFree(m->staging);
+    delete m;
+    return ORCHA_OK;
+}
+
+int32_t orcha_mesh_current(const orcha_mesh* m) { return m ? m->cur : -1; }
+
+orcha_status orcha_mesh_swap(orcha_mesh* m) {
+    if (!m) return fail(ORCHA_ERR_INVALID, "mesh_swap: null mesh");
+    m->cur ^= 1;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_set_tile(orcha_mesh* m, int32_t tx, int32_t ty) {
+    if (!m) return fail(ORCHA_ERR_INVALID, "mesh_set_tile: null mesh");
+    if (!orcha::hydro_tile_supported(m->dev.ndim, tx, ty))
+        return fail(ORCHA_ERR_UNSUPPORTED, "mesh_set_tile: no %dx%d tile variant", tx, ty);
+    if (m->dev.bs[0] % tx || m->dev.bs[1] % ty)
+        return fail(ORCHA_ERR_INVALID, "mesh_set_tile: %dx%d does not divide the block", tx, ty);
+    ORCHA_CUDA(orcha::configure_hydro(m->dev.ndim, tx, ty), "mesh_set_tile");
+    m->tile_x = tx;
+    m->tile_y = ty;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_get_tile(const orcha_mesh* m, int32_t* tx, int32_t* ty) {
+    if (!m || !tx || !ty) return fail(ORCHA_ERR_INVALID, "mesh_get_tile: null argument");
+    *tx = m->tile_x;
+    *ty = m->tile_y;
+    return ORCHA_OK;
+}
+
+static orcha_status ensure_staging(orcha_mesh* m) {
+    if (m->staging) return ORCHA_OK;
+    const size_t n = (size_t)m->nblk * m->dev.nvar * m->ncell;
+    ORCHA_CUDA(cudaMalloc(&m->staging, n * sizeof(double)), "staging buffer");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_load(orcha_mesh* m, const double* interior, int32_t host_ptr, void* stream) {
+    if (!m || !interior) return fail(ORCHA_ERR_INVALID, "mesh_load: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* src = interior;
+    if (host_ptr) {
+        orcha_status s = ensure_staging(m);
+        if (s) return s;
+        const size_t bytes = (size_t)m->nblk * m->dev.nvar * m->ncell * sizeof(double);
+        ORCHA_CUDA(cudaMemcpyAsync(m->staging, interior, bytes, cudaMemcpyHostToDevice, st), "mesh_load H2D");
+        src = m->staging;
+    }
+    ORCHA_CUDA(orcha::launch_pack(m->dev, src, m->desc.state_dev[m->cur], st), "mesh_load pack");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_store(orcha_mesh* m, double* interior, int32_t host_ptr, void* stream) {
+    if (!m || !interior) return fail(ORCHA_ERR_INVALID, "mesh_store: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (host_ptr) {
+        orcha_status s = ensure_staging(m);
+        if (s) return s;
+        ORCHA_CUDA(orcha::launch_unpack(m->dev, m->desc.state_dev[m->cur], m->staging, st), "mesh_store unpack");
+        const size_t bytes = (size_t)m->nblk * m->dev.nvar * m->ncell * sizeof(double);
+        ORCHA_CUDA(cudaMemcpyAsync(interior, m->staging, bytes, cudaMemcpyDeviceToHost, st), "mesh_store D2H");
+        return ORCHA_OK;
+    }
+    ORCHA_CUDA(orcha::launch_unpack(m->dev, m->desc.state_dev[m->cur], interior, st), "mesh_store unpack");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_packet_create(orcha_mesh* m, const int32_t* ids, int32_t n, orcha_packet** out) {
+    if (!m || !ids || !out) return fail(ORCHA_ERR_INVALID, "packet_create: null argument");
+    *out = nullptr;
+    if (n < 1) return fail(ORCHA_ERR_INVALID, "packet_create: empty packet");
+    if (n > m->nblk) return fail(ORCHA_ERR_INVALID, "packet_create: more ids than blocks");
+    std::vector<char> seen((size_t)m->nblk, 0);
+    for (int i = 0; i < n; ++i) {
+        if (ids[i] < 0 || ids[i] >= m->nblk)
+            return fail(ORCHA_ERR_INVALID, "packet_create: block id %d outside [0, %d)", ids[i], m->nblk);
+        if (seen[ids[i]]) return fail(ORCHA_ERR_INVALID, "packet_create: block id %d repeated", ids[i]);
+        seen[ids[i]] = 1;
+    }
+    orcha_packet* p = new orcha_packet();
+    p->mesh = m;
+    p->n = n;
+    cudaError_t e = cudaMalloc(&p->ids_dev, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(p->ids_dev, ids, sizeof(int) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->ids_dev);
+        delete p;
+        return cuda_fail(e, "packet_create");
+    }
+    *out = p;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_packet_destroy(orcha_packet* p) {
+    if (!p) return ORCHA_OK;
+    cudaDeviceSynchronize();
+    cudaFree(p->ids_dev);
+    delete p;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
+    if (!p) return fail(ORCHA_ERR_INVALID, "packet_run: null packet");
+    orcha_mesh* m = p->mesh;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* cur = m->desc.state_dev[m->cur];
+    double* nxt = m->desc.state_dev[m->cur ^ 1];
+    cudaError_t e;
+    switch (task) {
+        case ORCHA_TASK_GUARD_FILL: e = orcha::launch_guard_fill(m->dev, p->ids_dev, p->n, cur, st); break;
+        case ORCHA_TASK_HYDRO_FP64:
+        case ORCHA_TASK_HYDRO_F32FLUX:
+            e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, task == ORCHA_TASK_HYDRO_F32FLUX, p->ids_dev, p->n,
+                                    cur, nxt, st);
+            break;
+        case ORCHA_TASK_SIGNAL_SPEED: e = orcha::launch_signal_speed(m->dev, p->ids_dev, p->n, cur, st); break;
+        default: return fail(ORCHA_ERR_INVALID, "packet_run: unknown task %d", (int)task);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "packet_run launch");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_dt_reduce(orcha_mesh* m, void* stream) {
+    if (!m) return fail(ORCHA_ERR_INVALID, "dt_reduce: null mesh");
+    ORCHA_CUDA(orcha::launch_dt_reduce(m->dev, m->nblk, m->desc.dt_dev, (cudaStream_t)stream), "dt_reduce launch");
+    return ORCHA_OK;
+}
+
+static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int npk, orcha_task task, int nsteps,
+                                  int init_dt, void* stream) {
+    orcha_status s;
+    if (init_dt) {
+        for (int i = 0; i < npk; ++i)
+            if ((s = orcha_packet_run(pk[i], ORCHA_TASK_SIGNAL_SPEED, stream))) return s;
+        if ((s = orcha_dt_reduce(m, stream))) return s;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        for (int i = 0; i < npk; ++i)
+            if ((s = orcha_packet_run(pk[i], ORCHA_TASK_GUARD_FILL, stream))) return s;
+        for (int i = 0; i < npk; ++i)
+            if ((s = orcha_packet_run(pk[i], task, stream))) return s;
+        if ((s = orcha_dt_reduce(m, stream))) return s;
+        m->cur ^= 1;
+    }
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t npk, orcha_task task, int32_t nsteps,
+                                int32_t init_dt, int32_t use_graph, void* stream) {
+    if (!m || (!pk && npk > 0) || npk < 0 || nsteps < 0) return fail(ORCHA_ERR_INVALID, "mesh_advance: bad argument");
+    if (task != ORCHA_TASK_HYDRO_FP64 && task != ORCHA_TASK_HYDRO_F32FLUX)
+        return fail(ORCHA_ERR_INVALID, "mesh_advance: task must be a hydro task");
+    long long covered = 0;
+    for (int i = 0; i < npk; ++i) {
+        if (!pk[i] || pk[i]->mesh != m) return fail(ORCHA_ERR_INVALID, "mesh_advance: packet %d not of this mesh", i);
+        covered += pk[i]->n;
+    }
+    if (covered != m->nblk)
+        return fail(ORCHA_ERR_INVALID, "mesh_advance: packets cover %lld ids, the mesh has %d blocks", covered, m->nblk);
+    if (!use_graph) return enqueue_steps(m, pk, npk, task, nsteps, init_dt, stream);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st == nullptr) return fail(ORCHA_ERR_INVALID, "mesh_advance: graph capture needs a non-default stream");
+    const int start = m->cur;
+    for (auto& g : m->graphs) {
+        if (g.task == task && g.nsteps == nsteps && g.init_dt == init_dt && g.start_cur == start &&
+            g.packets.size() == (size_t)npk && std::equal(g.packets.begin(), g.packets.end(), pk)) {
+            ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
+            m->cur = start ^ (nsteps & 1);
+            return ORCHA_OK;
+        }
+    }
+    ORCHA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    orcha_status s = enqueue_steps(m, pk, npk, task, nsteps, init_dt, stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    m->cur = start;
+    if (s) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    GraphEntry g;
+    g.packets.assign(pk, pk + npk);
+    g.task = task;
+    g.nsteps = nsteps;
+    g.init_dt = init_dt;
+    g.start_cur = start;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    m->graphs.push_back(g);
+    ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
+    m->cur = start ^ (nsteps & 1);
+    return ORCHA_OK;
+}
+
+orcha_status orcha_mesh_poll(orcha_mesh* m, void* stream, int32_t* device_error) {
+    if (!m || !device_error) return fail(ORCHA_ERR_INVALID, "mesh_poll: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    ORCHA_CUDA(cudaStreamSynchronize(st), "mesh_poll sync");
+    int h = 0;
+    ORCHA_CUDA(cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost), "mesh_poll read");
+    ORCHA_CUDA(cudaMemset(m->err, 0, sizeof(int)), "mesh_poll clear");
+    *device_error = h;
+    if (h & ORCHA_DEVERR_TIMEOUT) return fail(ORCHA_ERR_TIMEOUT, "device wait timed out (error word %d)", h);
+    if (h) return fail(ORCHA_ERR_NONFINITE, "device reported a non-physical state (error word %d)", h);
+    return ORCHA_OK;
+}
+
+const char* orcha_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

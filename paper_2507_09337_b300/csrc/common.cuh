@@ -1,0 +1,109 @@
+// common.cuh -- device-side types shared by the block-hydro kernels.
+//
+// Arithmetic contract of the FP64 path: every operation is one IEEE-754
+// round-to-nearest operation and none is fused or reordered, so a kernel
+// that evaluates the same expression tree as the scheme's definition gets
+// the same bits. The `rd` type enforces this through the __d*_rn intrinsics,
+// which the compiler never contracts into FMAs. The FP32 flux path uses
+// plain float, where contraction is allowed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace orcha {
+
+constexpr int kGuard = 2;   // guard layers per side: the scheme's stencil reaches two cells
+
+// ---------------------------------------------------------------- FP64, never fused
+struct rd {
+    double v;
+    __device__ __forceinline__ rd() {}
+    __device__ __forceinline__ constexpr rd(double x) : v(x) {}
+};
+__device__ __forceinline__ rd operator+(rd a, rd b) { return rd(__dadd_rn(a.v, b.v)); }
+__device__ __forceinline__ rd operator-(rd a, rd b) { return rd(__dsub_rn(a.v, b.v)); }
+__device__ __forceinline__ rd operator*(rd a, rd b) { return rd(__dmul_rn(a.v, b.v)); }
+__device__ __forceinline__ rd operator-(rd a) { return rd(-a.v); }
+__device__ __forceinline__ bool operator<(rd a, rd b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator>(rd a, rd b) { return a.v > b.v; }
+__device__ __forceinline__ bool operator<=(rd a, rd b) { return a.v <= b.v; }
+__device__ __forceinline__ bool operator>=(rd a, rd b) { return a.v >= b.v; }
+
+// Precision traits: storage type, conversions, reciprocal, square root and
+// the sign tests the scheme uses. For rd every function is the correctly
+// rounded IEEE operation (1/x by __drcp_rn equals the IEEE quotient 1.0/x).
+template <class T> struct P;
+
+template <> struct P<rd> {
+    using store = double;
+    static __device__ __forceinline__ rd in(double x) { return rd(x); }
+    static __device__ __forceinline__ double out(rd x) { return x.v; }
+    static __device__ __forceinline__ rd rcp(rd x) { return rd(__drcp_rn(x.v)); }
+    static __device__ __forceinline__ rd sqrt(rd x) { return rd(__dsqrt_rn(x.v)); }
+    static __device__ __forceinline__ rd ld(const double* p) { return rd(*p); }
+    static __device__ __forceinline__ void st(double* p, rd x) { *p = x.v; }
+    static __device__ __forceinline__ bool pos(rd x) { return x.v > 0.0; }   // false for NaN
+    static __device__ __forceinline__ bool neg(rd x) { return x.v < 0.0; }
+    static __device__ __forceinline__ rd zero() { return rd(0.0); }
+    static __device__ __forceinline__ double to_double(rd x) { return x.v; }
+};
+
+template <> struct P<float> {
+    using store = float;
+    static __device__ __forceinline__ float in(double x) { return __double2float_rn(x); }
+    static __device__ __forceinline__ float out(float x) { return x; }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return __fsqrt_rn(x); }
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float x) { *p = x; }
+    static __device__ __forceinline__ bool pos(float x) { return x > 0.0f; }
+    static __device__ __forceinline__ bool neg(float x) { return x < 0.0f; }
+    static __device__ __forceinline__ float zero() { return 0.0f; }
+    static __device__ __forceinline__ double to_double(float x) { return (double)x; }
+};
+
+// ---------------------------------------------------------------- mesh as the kernels see it
+struct MeshDev {
+    int ndim, nvar;
+    int nb[3];          // blocks per axis
+    int bs[3];          // interior cells per block per axis
+    int pad[3];         // padded extents: bs + 2*kGuard on active axes, 1 otherwise
+    int periodic[3];
+    long long var_stride;   // pad[0]*pad[1]*pad[2]
+    long long blk_stride;   // nvar * var_stride
+    double gamma, gm1, igm1, cfl;   // gm1 = gamma - 1, igm1 = 1 / (gamma - 1), formed in FP64 on the host
+    double idx[3];          // 1 / dx_d
+    const double* dt;       // device: current time step
+    unsigned long long* smax;   // device: per-block largest signal speed (bits of a non-negative double)
+    int* err;               // device: error word (ORCHA_DEVERR_* bits)
+};
+
+// Largest of two non-negative doubles given as bit patterns (NaN patterns of
+// either sign compare above every finite value, so a NaN is never lost).
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Reduce a per-thread signal speed over the CTA and raise the block's entry.
+// `scratch` holds one word per warp. Every thread of the CTA must call it.
+__device__ __forceinline__ void cta_raise_smax(double s, unsigned long long* scratch,
+                                               unsigned long long* dst) {
+    unsigned long long b = warp_max_u64((unsigned long long)__double_as_longlong(s));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) scratch[warp] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = umax64(m, scratch[w]);
+        atomicMax(dst, m);
+    }
+}
+
+}  // namespace orcha

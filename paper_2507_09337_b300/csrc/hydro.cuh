@@ -1,0 +1,418 @@
+// hydro.cuh -- the fused block-hydro task kernel (one time step of a packet).
+//
+// Scheme (per cell, per step): primitives W from the conserved state U
+// (ideal gamma-law EOS), minmod slopes of W along each axis, a Hancock
+// half-step predictor in primitive form summed over all axes, face states
+// Wbar -+ dW/2 (a cell whose face states have rho <= 0 or p <= 0 falls back
+// to first order), HLL fluxes with Davis wave speeds, and the unsplit
+// conservative update U+ = U - sum_d (dt/dx_d)(F_hi - F_lo) summed x, y, z.
+// The epilogue raises the block's largest signal speed sum_d (|u_d|+c)/dx_d
+// of U+ (the next CFL time step). The paper's solver paragraph (section
+// "Experiments") describes the task only as explicit finite volume with
+// guard-cell halos refreshed before it runs; the expression trees below are
+// the ones of the FP64 definition, operation for operation.
+//
+// GPU mapping. One CTA owns a TX x TY column tile of one block and sweeps it
+// along z (2.5D blocking), one thread per interior column. Per plane:
+//   L  primitives of the (TX+4)(TY+4) plane two layers ahead into a ring of
+//      three planes in shared memory (the z stencil needs p-1, p, p+1);
+//   P  slopes, predictor and face states of plane p: interior cells by their
+//      owner thread (z face states stay in its registers), the one-cell ring
+//      around the tile by the first 2(TX+TY) threads (x/y face states only);
+//   F  every x and y face flux of plane p once, into shared memory;
+//   U  each owner forms its z face flux from registers, finishes the update
+//      of plane p-1 (whose z fluxes are now both known) and writes it.
+// Every face flux is evaluated exactly once per CTA and used by both cells,
+// so the update telescopes; tiles of one block recompute only their one-cell
+// ring of predicted states and their boundary faces.
+#pragma once
+
+#include "common.cuh"
+
+namespace orcha {
+
+// ---------------------------------------------------------------- point functions
+
+// W from U: r = 1/rho, u_d = m_d * r, p = (gamma-1) * (E - 0.5 * sum_d m_d u_d).
+template <class T, int NDIM>
+__device__ __forceinline__ void prim_from_cons(const T* U, T* W, T& r, T gm1) {
+    constexpr int NV = NDIM + 2;
+    W[0] = U[0];
+    r = P<T>::rcp(U[0]);
+    T mu;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        W[1 + d] = U[1 + d] * r;
+        mu = (d == 0) ? (U[1] * W[1]) : (mu + (U[1 + d] * W[1 + d]));
+    }
+    T ke = T(0.5) * mu;
+    W[NV - 1] = gm1 * (U[NV - 1] - ke);
+}
+
+// minmod: the smaller-magnitude argument when both share a strict sign, else 0.
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+    if (P<T>::pos(a) && P<T>::pos(b)) return (a < b) ? a : b;
+    if (P<T>::neg(a) && P<T>::neg(b)) return (a > b) ? a : b;
+    return P<T>::zero();
+}
+
+// Conserved state and physical flux of a primitive state given normal-first:
+// W = (rho, u_n, u_t1[, u_t2], p). |u|^2 is summed in coordinate order x, y, z;
+// for an x or y normal that is (u_n^2 + u_t1^2) + u_t2^2 (addition commutes),
+// for a z normal (u_t1^2 + u_t2^2) + u_n^2.
+template <class T, int NDIM, bool ZNORMAL>
+__device__ __forceinline__ void cons_flux(const T* W, T* U, T* F, T igm1) {
+    constexpr int NV = NDIM + 2;
+    const T rho = W[0], un = W[1], p = W[NV - 1];
+    U[0] = rho;
+#pragma unroll
+    for (int k = 1; k <= NDIM; ++k) U[k] = rho * W[k];
+    T q2;
+    if (NDIM == 2) q2 = (W[1] * W[1]) + (W[2] * W[2]);
+    else if (!ZNORMAL) q2 = ((W[1] * W[1]) + (W[2] * W[2])) + (W[3] * W[3]);
+    else q2 = ((W[2] * W[2]) + (W[3] * W[3])) + (W[1] * W[1]);
+    U[NV - 1] = (p * igm1) + ((T(0.5) * rho) * q2);
+    F[0] = U[1];
+    F[1] = (U[1] * un) + p;
+#pragma unroll
+    for (int k = 2; k <= NDIM; ++k) F[k] = U[k] * un;
+    F[NV - 1] = (U[NV - 1] + p) * un;
+}
+
+// HLL flux with Davis wave speeds between normal-first states L and R.
+template <class T, int NDIM, bool ZNORMAL>
+__device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
+    constexpr int NV = NDIM + 2;
+    const T cL = P<T>::sqrt((g * L[NV - 1]) * P<T>::rcp(L[0]));
+    const T cR = P<T>::sqrt((g * R[NV - 1]) * P<T>::rcp(R[0]));
+    T a = L[1] - cL, b = R[1] - cR;
+    const T SL = (a < b) ? a : b;
+    a = L[1] + cL;
+    b = R[1] + cR;
+    const T SR = (a > b) ? a : b;
+    T UL[NV], UR[NV], FL[NV], FR[NV];
+    cons_flux<T, NDIM, ZNORMAL>(L, UL, FL, igm1);
+    cons_flux<T, NDIM, ZNORMAL>(R, UR, FR, igm1);
+    if (SL >= T(0.0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FL[v];
+    } else if (SR <= T(0.0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FR[v];
+    } else {
+        const T slsr = SL * SR;
+        const T inv = P<T>::rcp(SR - SL);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = (((SR * FL[v]) - (SL * FR[v])) + (slsr * (UR[v] - UL[v]))) * inv;
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <int NDIM, int TX, int TY>
+struct Tile {
+    static constexpr int NV = NDIM + 2;
+    static constexpr int NW = NV + 1;                 // primitives + 1/rho
+    static constexpr int NT = TX * TY;                // threads = interior columns
+    static constexpr int R2X = TX + 4, R2Y = TY + 4, R2N = R2X * R2Y;
+    static constexpr int R1X = TX + 2, R1Y = TY + 2, R1N = R1X * R1Y;
+    static constexpr int NRING = 2 * (TX + TY);       // predicted ring cells (corners unused)
+    static constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    static constexpr int NSLOT = (NDIM == 3) ? 3 : 1;
+    template <class S>
+    static constexpr size_t smem_bytes() {
+        return sizeof(S) * ((size_t)NSLOT * NW * R2N + 4 * NV * R1N + NV * (NXF + NYF));
+    }
+};
+
+template <int NDIM, int TX, int TY, class T>
+__global__ void __launch_bounds__(TX * TY)
+hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
+             const double* __restrict__ Uin, double* __restrict__ Uout) {
+    using Tl = Tile<NDIM, TX, TY>;
+    using S = typename P<T>::store;
+    constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
+    constexpr int R2X = Tl::R2X, R2N = Tl::R2N, R1X = Tl::R1X, R1N = Tl::R1N;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* sW = reinterpret_cast<S*>(smem_raw);                 // [slot][NW][R2N]
+    S* sFS = sW + Tl::NSLOT * NW * R2N;                    // [face 0..3 = x-,x+,y-,y+][NV][R1N]
+    S* sFx = sFS + 4 * NV * R1N;                           // [NV][NXF]
+    S* sFy = sFx + NV * Tl::NXF;                           // [NV][NYF]
+    __shared__ unsigned long long red[32];
+
+    const int tid = threadIdx.x;
+    const int ntile = tiles_x * tiles_y;
+    const int blk = blk_ids[blockIdx.x / ntile];
+    const int tile = blockIdx.x % ntile;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    const int px = m.pad[0], py = m.pad[1];
+    const long long vs = m.var_stride;
+    const double* Ub = Uin + (long long)blk * m.blk_stride;
+    double* Ob = Uout + (long long)blk * m.blk_stride;
+    const int bz = (NDIM == 3) ? m.bs[2] : 1;
+
+    const T g = P<T>::in(m.gamma), gm1 = P<T>::in(m.gm1), igm1 = P<T>::in(m.igm1);
+    const double dt = *m.dt;
+    double cd[3];
+    T hd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cd[d] = __dmul_rn(dt, m.idx[d]);              // dt / dx_d
+        hd[d] = P<T>::in(__dmul_rn(0.5, cd[d]));      // (dt/2) / dx_d
+    }
+
+    // owner column of this thread
+    const int ti = tid % TX, tj = tid / TX;
+    const int o2 = (tj + 2) * R2X + (ti + 2);       // in the R2 plane
+    const int o1 = (tj + 1) * R1X + (ti + 1);       // in the R1 plane
+    // ring cell of this thread (tid < NRING): bottom row, top row, left column, right column
+    int rc1 = 0, rc2 = 0, rface = 0;
+    if (tid < Tl::NRING) {
+        int ci, cj;
+        if (tid < TX) { ci = tid + 1; cj = 0; rface = 3; }                      // row -1: needs y+
+        else if (tid < 2 * TX) { ci = tid - TX + 1; cj = TY + 1; rface = 2; }   // row TY: needs y-
+        else if (tid < 2 * TX + TY) { ci = 0; cj = tid - 2 * TX + 1; rface = 1; }       // col -1: x+
+        else { ci = TX + 1; cj = tid - 2 * TX - TY + 1; rface = 0; }            // col TX: x-
+        rc1 = cj * R1X + ci;
+        rc2 = (cj + 1) * R2X + (ci + 1);
+    }
+
+    // L: primitives of plane pz (interior z index, -2 .. bz+1) into its ring slot
+    auto load_plane = [&](int pzi) {
+        const int slot = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
+        S* w = sW + slot * NW * R2N;
+        const int zz = (NDIM == 3) ? pzi + kGuard : 0;
+        for (int c = tid; c < R2N; c += NT) {
+            const int ci = c % R2X, cj = c / R2X;
+            const long long gi = ((long long)zz * py + (y0 + cj)) * px + (x0 + ci);
+            T U[NV], W[NV], r;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) U[v] = P<T>::in(Ub[gi + v * vs]);
+            prim_from_cons<T, NDIM>(U, W, r, gm1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
+            P<T>::st(&w[NV * R2N + c], r);
+            const bool interior = ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2 && pzi >= 0 && pzi < bz;
+            if (interior && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1]))) atomicOr(m.err, 1);
+        }
+    };
+
+    // P: slopes, predictor and face states of the cell at R2 index c2 of plane
+    // pzi; writes flo/fhi (face states on the low/high side along each axis).
+    auto predict = [&](int pzi, int c2, T (&flo)[3][NV], T (&fhi)[3][NV]) {
+        const int sc = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
+        const S* w = sW + sc * NW * R2N;
+        T Wc[NV], dW[3][NV], a[3][NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Wc[v] = P<T>::ld(&w[v * R2N + c2]);
+        const T rc = P<T>::ld(&w[NV * R2N + c2]);
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const S* wm;
+            const S* wp;
+            int cm = c2, cp = c2;
+            if (d == 0) { cm = c2 - 1; cp = c2 + 1; wm = w; wp = w; }
+            else if (d == 1) { cm = c2 - R2X; cp = c2 + R2X; wm = w; wp = w; }
+            else {
+                wm = sW + ((pzi + 2) % 3) * NW * R2N;     // plane pzi-1
+                wp = sW + ((pzi + 4) % 3) * NW * R2N;     // plane pzi+1
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T dl = Wc[v] - P<T>::ld(&wm[v * R2N + cm]);
+                const T dr = P<T>::ld(&wp[v * R2N + cp]) - Wc[v];
+                dW[d][v] = minmod(dl, dr);
+            }
+        }
+        const T gp = g * Wc[NV - 1];
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const T un = Wc[1 + d], dun = dW[d][1 + d], dp = dW[d][NV - 1];
+            a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);
+#pragma unroll
+            for (int t = 0; t < NDIM; ++t)
+                a[d][1 + t] = (t == d) ? ((un * dun) + (dp * rc)) : (un * dW[d][1 + t]);
+            a[d][NV - 1] = (gp * dun) + (un * dp);
+        }
+        T Wb[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            T s = hd[0] * a[0][v];
+#pragma unroll
+            for (int d = 1; d < NDIM; ++d) s = s + (hd[d] * a[d][v]);
+            Wb[v] = Wc[v] - s;
+        }
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T hs = T(0.5) * dW[d][v];
+                flo[d][v] = Wb[v] - hs;
+                fhi[d][v] = Wb[v] + hs;
+            }
+            ok = ok && P<T>::pos(flo[d][0]) && P<T>::pos(flo[d][NV - 1]) && P<T>::pos(fhi[d][0]) &&
+                 P<T>::pos(fhi[d][NV - 1]);
+        }
+        if (!ok) {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { flo[d][v] = Wc[v]; fhi[d][v] = Wc[v]; }
+        }
+    };
+
+    // z state carried by the owner: high-z face state of the previous plane,
+    // its low-z face flux, and its x+y flux sum
+    T zp_prev[NV], Fz_prev[NV];
+    double acc_prev[NV];
+    double smax = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { zp_prev[v] = P<T>::zero(); Fz_prev[v] = P<T>::zero(); acc_prev[v] = 0.0; }
+
+    const int pbeg = (NDIM == 3) ? -1 : 0, pend = (NDIM == 3) ? bz : 0;
+    if (NDIM == 3) { load_plane(-2); load_plane(-1); }
+
+    for (int p = pbeg; p <= pend; ++p) {
+        const bool inner = p >= 0 && p < bz;       // plane p is interior: it has x/y faces to flux
+        if (NDIM == 3) load_plane(p + 1);
+        else load_plane(0);
+        __syncthreads();
+
+        // ---- P: predict
+        T zlo[NV], zhi[NV];
+        {
+            T flo[3][NV], fhi[3][NV];
+            predict(p, o2, flo, fhi);
+            if (inner) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
+                    P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
+                    P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
+                    P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
+                }
+            }
+            if (NDIM == 3) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
+            }
+        }
+        if (inner && tid < Tl::NRING) {
+            T flo[3][NV], fhi[3][NV];
+            predict(p, rc2, flo, fhi);
+            const int d = rface >> 1;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], (rface & 1) ? fhi[d][v] : flo[d][v]);
+        }
+        __syncthreads();
+
+        // ---- F: x and y face fluxes of plane p
+        if (inner) {
+            for (int f = tid; f < Tl::NXF + Tl::NYF; f += NT) {
+                int iL, iR, fL, fR, nrm;
+                if (f < Tl::NXF) {
+                    const int fi = f % (TX + 1), fj = f / (TX + 1);
+                    iL = (fj + 1) * R1X + fi; iR = iL + 1; fL = 1; fR = 0; nrm = 0;
+                } else {
+                    const int f2 = f - Tl::NXF;
+                    const int fi = f2 % TX, fj = f2 / TX;
+                    iL = fj * R1X + fi + 1; iR = iL + R1X; fL = 3; fR = 2; nrm = 1;
+                }
+                T L[NV], R[NV], F[NV];
+                // normal-first order: (rho, u_n, u_t..., p)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    int src = v;
+                    if (v == 1) src = 1 + nrm;
+                    else if (v == 2 && nrm == 1) src = 1;
+                    L[v] = P<T>::ld(&sFS[(fL * NV + src) * R1N + iL]);
+                    R[v] = P<T>::ld(&sFS[(fR * NV + src) * R1N + iR]);
+                }
+                hll<T, NDIM, false>(L, R, F, g, igm1);
+                S* dst = (nrm == 0) ? (sFx + f) : (sFy + (f - Tl::NXF));
+                const int stride = (nrm == 0) ? Tl::NXF : Tl::NYF;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    int dv = v;
+                    if (v == 1) dv = 1 + nrm;
+                    else if (v == 2 && nrm == 1) dv = 1;
+                    P<T>::st(&dst[dv * stride], F[v]);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- U: z flux, update of the finished plane, x+y sums of this plane
+        if (NDIM == 3) {
+            T Fz[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Fz[v] = P<T>::zero();
+            if (p >= 0) {
+                T L[NV], R[NV];
+                L[0] = zp_prev[0]; L[1] = zp_prev[3]; L[2] = zp_prev[1]; L[3] = zp_prev[2]; L[4] = zp_prev[4];
+                R[0] = zlo[0]; R[1] = zlo[3]; R[2] = zlo[1]; R[3] = zlo[2]; R[4] = zlo[4];
+                T F[NV];
+                hll<T, NDIM, true>(L, R, F, g, igm1);
+                Fz[0] = F[0]; Fz[3] = F[1]; Fz[1] = F[2]; Fz[2] = F[3]; Fz[4] = F[4];
+            }
+            if (p >= 1) {
+                const int q = p - 1;
+                const long long gi = ((long long)(q + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                rd Un[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
+                    const rd acc = rd(acc_prev[v]) + tz;
+                    Un[v] = rd(Ub[gi + v * vs]) - acc;
+                    Ob[gi + v * vs] = Un[v].v;
+                }
+                // signal speed of the new state
+                rd W[NV], r;
+                prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
+                if (!(W[0].v > 0.0 && W[NV - 1].v > 0.0)) atomicOr(m.err, 1);
+                const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
+                rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
+#pragma unroll
+                for (int d = 1; d < NDIM; ++d) s = s + ((rd(fabs(W[1 + d].v)) + c) * rd(m.idx[d]));
+                smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
+        }
+        if (inner) {
+            // x then y flux differences of plane p (FP64)
+            const int fx = tj * (TX + 1) + ti, fy = tj * TX + ti;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx + 1]))) -
+                                           rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx]))));
+                const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy + TX]))) -
+                                           rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy]))));
+                acc_prev[v] = (tx + ty).v;
+            }
+            if (NDIM == 2) {
+                const long long gi = ((long long)(y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                rd Un[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
+                    Ob[gi + v * vs] = Un[v].v;
+                }
+                rd W[NV], r;
+                prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
+                if (!(W[0].v > 0.0 && W[NV - 1].v > 0.0)) atomicOr(m.err, 1);
+                const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
+                rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
+                s = s + ((rd(fabs(W[2].v)) + c) * rd(m.idx[1]));
+                smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+            }
+        }
+    }
+    cta_raise_smax(smax, red, &m.smax[blk]);
+}
+
+}  // namespace orcha

@@ -1,0 +1,219 @@
+// kernels.cu -- guard fill, pack/unpack, signal speed and dt reduction, and
+// the launch table of the hydro kernel variants.
+#include <cstdio>
+
+#include "common.cuh"
+#include "hydro.cuh"
+#include "launch.h"
+
+namespace orcha {
+
+// ---------------------------------------------------------------- guard fill
+// Guard cells of block b (padded index outside the interior box) take the
+// value of the global cell at the same position, with the boundary rule on
+// the domain edge: outflow clamps the index to [0, N-1] on each axis
+// (zero-gradient; faces, edges and corners alike), periodic wraps it. The
+// source is always an interior cell of some block in the same buffer, so
+// guard writes never race with the reads.
+__device__ __forceinline__ int map_axis(int gi, int n, int periodic) {
+    if (periodic) { gi %= n; return gi < 0 ? gi + n : gi; }
+    return gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+}
+
+__global__ void guard_fill_kernel(const MeshDev m, const int* __restrict__ blk_ids, double* __restrict__ U) {
+    const long long npad = m.var_stride;
+    const int pb = blockIdx.y;
+    const int blk = blk_ids[pb];
+    const int b[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < npad;
+         c += (long long)gridDim.x * blockDim.x) {
+        int loc[3] = {(int)(c % m.pad[0]), (int)((c / m.pad[0]) % m.pad[1]), (int)(c / ((long long)m.pad[0] * m.pad[1]))};
+        bool guard = false;
+        int src_blk[3], src_loc[3];
+        for (int d = 0; d < 3; ++d) {
+            if (d >= m.ndim) { src_blk[d] = 0; src_loc[d] = 0; continue; }
+            const int li = loc[d] - kGuard;                 // interior-relative index
+            if (li < 0 || li >= m.bs[d]) guard = true;
+            const int n = m.nb[d] * m.bs[d];
+            const int gi = map_axis(b[d] * m.bs[d] + li, n, m.periodic[d]);
+            src_blk[d] = gi / m.bs[d];
+            src_loc[d] = gi % m.bs[d] + kGuard;
+        }
+        if (!guard) continue;
+        const long long sb = src_blk[0] + (long long)m.nb[0] * (src_blk[1] + (long long)m.nb[1] * src_blk[2]);
+        const int sz = (m.ndim == 3) ? src_loc[2] : 0;
+        const long long so = sb * m.blk_stride + ((long long)sz * m.pad[1] + src_loc[1]) * m.pad[0] + src_loc[0];
+        const long long dof = (long long)blk * m.blk_stride + c;
+        for (int v = 0; v < m.nvar; ++v) U[dof + v * npad] = U[so + v * npad];
+    }
+}
+
+// ---------------------------------------------------------------- pack / unpack
+// Interior array [block][var][k][j][i] <-> padded state interior.
+__device__ __forceinline__ long long padded_offset(const MeshDev& m, long long e, long long ncell) {
+    const long long bv = e / ncell;               // block * nvar + var
+    const long long c = e % ncell;
+    const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+    const int kk = (m.ndim == 3) ? k + kGuard : 0;
+    return bv * m.var_stride + ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+}
+
+__global__ void pack_kernel(const MeshDev m, const double* __restrict__ interior, double* __restrict__ U) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        U[padded_offset(m, e, ncell)] = interior[e];
+}
+
+__global__ void unpack_kernel(const MeshDev m, const double* __restrict__ U, double* __restrict__ interior) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        interior[e] = U[padded_offset(m, e, ncell)];
+}
+
+// ---------------------------------------------------------------- signal speed of the current state
+__global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk_ids, const double* __restrict__ U) {
+    __shared__ unsigned long long red[32];
+    const int blk = blk_ids[blockIdx.x];
+    const double* Ub = U + (long long)blk * m.blk_stride;
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    double smax = 0.0;
+    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+        const int kk = (m.ndim == 3) ? k + kGuard : 0;
+        const long long po = ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+        rd Uc[5], W[5], r;
+        for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
+        if (m.ndim == 3) prim_from_cons<rd, 3>(Uc, W, r, rd(m.gm1));
+        else prim_from_cons<rd, 2>(Uc, W, r, rd(m.gm1));
+        const int nv = m.nvar;
+        if (!(W[0].v > 0.0 && W[nv - 1].v > 0.0)) atomicOr(m.err, 1);
+        const rd cs = P<rd>::sqrt((rd(m.gamma) * W[nv - 1]) * r);
+        rd s = (rd(fabs(W[1].v)) + cs) * rd(m.idx[0]);
+        for (int d = 1; d < m.ndim; ++d) s = s + ((rd(fabs(W[1 + d].v)) + cs) * rd(m.idx[d]));
+        smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+    }
+    cta_raise_smax(smax, red, &m.smax[blk]);
+}
+
+// ---------------------------------------------------------------- dt reduction
+// dt = cfl / max over blocks; then clear the per-block maxima for the next step.
+__global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__ dt) {
+    __shared__ unsigned long long red[32];
+    __shared__ unsigned long long total;
+    unsigned long long b = 0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) b = umax64(b, m.smax[i]);
+    b = warp_max_u64(b);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = umax64(t, red[w]);
+        total = t;
+        const double s = __longlong_as_double((long long)t);
+        if (s > 0.0 && s <= 1.7976931348623157e308) *dt = m.cfl / s;
+        else atomicOr(m.err, 2);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) m.smax[i] = 0ull;
+}
+
+// ---------------------------------------------------------------- hydro launch table
+template <int NDIM, int TX, int TY, class T>
+static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,
+                                  cudaStream_t st) {
+    using Tl = Tile<NDIM, TX, TY>;
+    const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
+    auto kern = hydro_kernel<NDIM, TX, TY, T>;
+    const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
+    kern<<<dim3((unsigned)(n * tx * ty)), dim3(TX * TY), smem, st>>>(m, ids, tx, ty, Uin, Uout);
+    return cudaGetLastError();
+}
+
+template <int NDIM, int TX, int TY, class T>
+static cudaError_t configure_t() {
+    using Tl = Tile<NDIM, TX, TY>;
+    const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
+    return cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+#define ORCHA_TILE_CASE(ND, X, Y)                                                                      \
+    if (ndim == ND && tx == X && ty == Y)                                                              \
+        return f32 ? launch_hydro_t<ND, X, Y, float>(m, ids, n, Uin, Uout, st)                         \
+                   : launch_hydro_t<ND, X, Y, rd>(m, ids, n, Uin, Uout, st);
+
+cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* ids, int n, const double* Uin,
+                         double* Uout, cudaStream_t st) {
+    const int ndim = m.ndim;
+    ORCHA_TILE_CASE(2, 8, 8)
+    ORCHA_TILE_CASE(2, 16, 8)
+    ORCHA_TILE_CASE(2, 16, 16)
+    ORCHA_TILE_CASE(3, 8, 8)
+    ORCHA_TILE_CASE(3, 16, 8)
+    ORCHA_TILE_CASE(3, 16, 16)
+    return cudaErrorInvalidConfiguration;
+}
+
+#define ORCHA_CONF_CASE(ND, X, Y)                                                                      \
+    if (ndim == ND && tx == X && ty == Y) {                                                            \
+        cudaError_t e = configure_t<ND, X, Y, float>();                                                \
+        return e != cudaSuccess ? e : configure_t<ND, X, Y, rd>();                                     \
+    }
+
+cudaError_t configure_hydro(int ndim, int tx, int ty) {
+    ORCHA_CONF_CASE(2, 8, 8)
+    ORCHA_CONF_CASE(2, 16, 8)
+    ORCHA_CONF_CASE(2, 16, 16)
+    ORCHA_CONF_CASE(3, 8, 8)
+    ORCHA_CONF_CASE(3, 16, 8)
+    ORCHA_CONF_CASE(3, 16, 16)
+    return cudaErrorInvalidConfiguration;
+}
+
+bool hydro_tile_supported(int ndim, int tx, int ty) {
+    const int t[3][2] = {{8, 8}, {16, 8}, {16, 16}};
+    for (auto& p : t)
+        if (p[0] == tx && p[1] == ty) return ndim == 2 || ndim == 3;
+    return false;
+}
+
+cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U, cudaStream_t st) {
+    const int threads = 256;
+    const long long npad = m.var_stride;
+    const unsigned gx = (unsigned)((npad + threads - 1) / threads);
+    guard_fill_kernel<<<dim3(gx, (unsigned)n), threads, 0, st>>>(m, ids, U);
+    return cudaGetLastError();
+}
+
+static unsigned copy_grid(const MeshDev& m, int threads) {
+    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * m.bs[0] * m.bs[1] * m.bs[2];
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    return (unsigned)blocks;
+}
+
+cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cudaStream_t st) {
+    pack_kernel<<<copy_grid(m, 256), 256, 0, st>>>(m, interior, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st) {
+    unpack_kernel<<<copy_grid(m, 256), 256, 0, st>>>(m, U, interior);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st) {
+    signal_speed_kernel<<<(unsigned)n, 256, 0, st>>>(m, ids, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st) {
+    dt_reduce_kernel<<<1, 1024, 0, st>>>(m, nblk, dt);
+    return cudaGetLastError();
+}
+
+}  // namespace orcha

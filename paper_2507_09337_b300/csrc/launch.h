@@ -1,0 +1,22 @@
+// launch.h -- host-side entry points of the kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace orcha {
+
+cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* ids, int n, const double* Uin,
+                         double* Uout, cudaStream_t st);
+bool hydro_tile_supported(int ndim, int tx, int ty);
+// Set the dynamic shared-memory limit of both precisions of a tile variant on
+// the current device (call once per device before launching or capturing).
+cudaError_t configure_hydro(int ndim, int tx, int ty);
+cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U, cudaStream_t st);
+cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cudaStream_t st);
+cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st);
+cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
+cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
+
+}  // namespace orcha

@@ -1,0 +1,66 @@
+"""Helpers for the GPU tests: run the CUDA path through the C ABI and compare
+with the oracle under the parity rule."""
+import numpy as np
+
+from paper_2507_09337_b300 import binding as B
+from paper_2507_09337_b300 import workloads as wl
+
+
+def rule12_error(G: np.ndarray, O: np.ndarray, nvar: int) -> float:
+    """Largest |g - o| / max(|o|, s_v) over cells and variables, where s_v is the
+    field's largest |momentum| for momentum components and |o| alone for rho
+    and E (a plain relative error is meaningless where momentum is zero by
+    symmetry). Arrays are block arrays [block, var, ...]."""
+    G = np.asarray(G)
+    O = np.asarray(O)
+    err = 0.0
+    mom = np.abs(O[:, 1:nvar - 1]).max() if nvar > 2 else 0.0
+    for v in range(nvar):
+        o, g = O[:, v], G[:, v]
+        scale = np.abs(o)
+        if 0 < v < nvar - 1:
+            scale = np.maximum(scale, mom)
+        d = np.abs(g - o)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.where(d == 0, 0.0, d / scale)
+        err = max(err, float(np.nanmax(r)) if r.size else 0.0)
+        if not np.all(np.isfinite(g)):
+            return float("inf")
+    return err
+
+
+def gpu_steps(spec, U0, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, packets=None, tile=None, use_graph=False,
+              record_dt=False):
+    """Run nsteps on the GPU; returns (U, dts or None, device error word)."""
+    import torch
+    mesh = B.Mesh(spec, packets=packets)
+    try:
+        if tile is not None:
+            mesh.set_tile(*tile)
+        mesh.load(U0)
+        dts = []
+        stream = torch.cuda.current_stream()
+        if record_dt:
+            mesh.run(B.ORCHA_TASK_SIGNAL_SPEED)
+            B.orcha_dt_reduce(mesh.handle)
+            for _ in range(nsteps):
+                dts.append(mesh.dt_value())
+                mesh.run(B.ORCHA_TASK_GUARD_FILL)
+                mesh.run(task)
+                B.orcha_dt_reduce(mesh.handle)
+                B.orcha_mesh_swap(mesh.handle)
+        else:
+            s = torch.cuda.Stream() if use_graph else stream
+            with torch.cuda.stream(s):
+                mesh.advance(nsteps, task, init_dt=True, use_graph=use_graph, stream=s)
+            s.synchronize()
+        err = mesh.poll()
+        return mesh.store(), (np.array(dts) if record_dt else None), err
+    finally:
+        mesh.close()
+
+
+def oracle_steps(oracle_mod, spec, U0, nsteps):
+    m = oracle_mod.Mesh(**spec.oracle_kwargs())
+    U, dts, _ = oracle_mod.run(m, U0, nsteps)
+    return U, dts
