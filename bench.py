@@ -209,29 +209,24 @@ def main():
     stream = torch.cuda.Stream(dev)
     npk = len(mesh.packets)
     h = mesh.handle
+    batch = B.orcha_batch_create(mesh.packets)
     hydro_events = []
-    launches_per_step = 1 + npk + 1 + nt * (2 * npk + 1) + 1
+    # per bench step: pack, signal speed of every packet, dt reduce, nt persistent launches, unpack
+    launches_per_step = 1 + npk + 1 + nt + 1
 
     def step(record: bool):
         B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
-        for p in mesh.packets:
-            B.orcha_packet_run(p, B.ORCHA_TASK_SIGNAL_SPEED, stream)
-        B.orcha_dt_reduce(h, stream)
+        B.orcha_batch_advance(batch, task, 0, True, False, stream)          # dt of the initial state
         for _ in range(nt):
-            for p in mesh.packets:
-                B.orcha_packet_run(p, B.ORCHA_TASK_GUARD_FILL, stream)
-            for i, p in enumerate(mesh.packets):
-                if record:
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    B.orcha_packet_run(p, task, stream)
-                    e1.record(stream)
-                    hydro_events.append((e0, e1, len(packets[i])))
-                else:
-                    B.orcha_packet_run(p, task, stream)
-            B.orcha_dt_reduce(h, stream)
-            B.orcha_mesh_swap(h)
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.orcha_batch_advance(batch, task, 1, False, False, stream)
+                e1.record(stream)
+                hydro_events.append((e0, e1, spec.nblocks))
+            else:
+                B.orcha_batch_advance(batch, task, 1, False, False, stream)
         B.orcha_mesh_store(h, out_dev.data_ptr(), False, stream)
 
     with torch.cuda.stream(stream):
@@ -281,14 +276,14 @@ def main():
         achieved = FLOPS_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "hydro_kernel<3,16,16,rd>", "per_launch": "one packet of 64 blocks (262144 zones)",
+                "kernel": "persistent_kernel<3,16,16,rd>", "per_launch": "one time step of all packets",
                 "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
     else:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
         achieved = BYTES_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "hydro_kernel<3,16,16,float>"}
+                "traffic": None, "kernel": "persistent_kernel<3,16,16,float>"}
     hbm_peak = 6489.3
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -303,7 +298,7 @@ def main():
 
     def e2e_step():
         B.orcha_mesh_load(h, U0_pin.data_ptr(), True, stream)
-        B.orcha_mesh_advance(h, mesh.packets, task, nt, True, True, stream)
+        B.orcha_batch_advance(batch, task, nt, True, True, stream)
         B.orcha_mesh_store(h, out_pin.data_ptr(), True, stream)
 
     with torch.cuda.stream(stream):
@@ -340,7 +335,7 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_io,
-                "d2h_bytes_per_step": bytes_io, "api": "orcha_mesh_load(host) + orcha_mesh_advance(graph) + "
+                "d2h_bytes_per_step": bytes_io, "api": "orcha_mesh_load(host) + orcha_batch_advance(graph) + "
                                                          "orcha_mesh_store(host)"},
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -348,6 +343,7 @@ def main():
         rate, cores, n, el = oracle_rate(spec, U0_host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{n} time steps of the full {spec.zones}-zone mesh in {el:.1f} s"}
+    B.orcha_batch_destroy(batch)
     mesh.close()
     if rank == 0:
         print(json.dumps(line))

@@ -175,6 +175,33 @@ ORCHA_API orcha_status orcha_mesh_advance(orcha_mesh* mesh, orcha_packet* const*
                                 orcha_task hydro_task, int32_t nsteps, int32_t init_dt,
                                 int32_t use_graph, void* stream);
 
+/* ------------------------------------------------------------------ batches
+ * A batch is a fixed set of packets (of one or more meshes) whose steps run
+ * as ONE persistent launch per time step: resident CTAs drain a device work
+ * queue of (mesh, block, column tile) items, read each tile's halo directly
+ * from the neighbouring blocks (no guard-fill pass; the padded guard layers
+ * are left untouched), and the CTA finishing a mesh's last item forms that
+ * mesh's next dt and flips its current buffer on the device. The packets of
+ * each mesh in the batch must cover all of its blocks exactly once. All
+ * meshes need the same ndim, and the tile must divide every mesh's blocks. */
+typedef struct orcha_batch orcha_batch;
+
+/* tx = ty = 0 picks the widest built tile that divides every mesh's blocks.
+ * Errors: INVALID (coverage, mixed ndim, tile does not divide), UNSUPPORTED,
+ * OOM, CUDA. The packets and meshes must outlive the batch. */
+ORCHA_API orcha_status orcha_batch_create(orcha_packet* const* packets, int32_t npackets, int32_t tx, int32_t ty,
+                                          orcha_batch** out);
+ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
+
+/* nsteps steps of every mesh in the batch on `stream`. init_dt != 0 first
+ * forms each mesh's dt from its current state (signal-speed task + dt
+ * reduce); otherwise each mesh's dt_dev must already hold its time step.
+ * use_graph != 0 captures the nsteps launches once per (task, nsteps) and
+ * replays the graph (needs a non-default stream). After the call each
+ * mesh's current buffer is the one its last step wrote. */
+ORCHA_API orcha_status orcha_batch_advance(orcha_batch* batch, orcha_task hydro_task, int32_t nsteps,
+                                           int32_t init_dt, int32_t use_graph, void* stream);
+
 /* Wait for `stream`, then read the device error word into *device_error (0 =
  * none) and clear it. Returns NONFINITE / TIMEOUT when a bit is set. */
 ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* device_error);

@@ -79,6 +79,9 @@ SIGNATURES = {
     "orcha_packet_run": (_st, [_vp, ctypes.c_int, _vp]),
     "orcha_dt_reduce": (_st, [_vp, _vp]),
     "orcha_mesh_advance": (_st, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _i32, _i32, _i32, _vp]),
+    "orcha_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    "orcha_batch_destroy": (_st, [_vp]),
+    "orcha_batch_advance": (_st, [_vp, ctypes.c_int, _i32, _i32, _i32, _vp]),
     "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
@@ -178,6 +181,22 @@ def orcha_mesh_advance(mesh: int, packets, task: int, nsteps: int, init_dt: bool
     arr = (_vp * len(packets))(*packets)
     _check(lib().orcha_mesh_advance(mesh, arr, len(packets), int(task), int(nsteps), int(bool(init_dt)),
                                     int(bool(use_graph)), _stream_ptr(stream)))
+
+
+def orcha_batch_create(packets, tx: int = 0, ty: int = 0) -> int:
+    arr = (_vp * len(packets))(*packets)
+    h = _vp()
+    _check(lib().orcha_batch_create(arr, len(packets), tx, ty, ctypes.byref(h)))
+    return h.value
+
+
+def orcha_batch_destroy(batch: int) -> None:
+    _check(lib().orcha_batch_destroy(batch))
+
+
+def orcha_batch_advance(batch: int, task: int, nsteps: int, init_dt: bool, use_graph: bool, stream=None) -> None:
+    _check(lib().orcha_batch_advance(batch, int(task), int(nsteps), int(bool(init_dt)), int(bool(use_graph)),
+                                     _stream_ptr(stream)))
 
 
 def orcha_mesh_poll(mesh: int, stream=None) -> int:

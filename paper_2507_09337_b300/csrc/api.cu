@@ -67,6 +67,22 @@ struct orcha_packet {
     orcha_mesh* mesh;
     int n;
     int* ids_dev;
+    std::vector<int> ids;
+};
+
+struct orcha_batch {
+    std::vector<orcha_mesh*> meshes;                 // one slot per mesh
+    std::vector<const orcha_packet*> packets;
+    int ndim = 3, tx = 8, ty = 8;
+    int nitems = 0;
+    orcha::SlotDev* slots_dev = nullptr;
+    orcha::Item* items_dev = nullptr;
+    unsigned* queue = nullptr;
+    unsigned* done_dev = nullptr;
+    int* cur_dev = nullptr;
+    int num_sms = 0;
+    struct G { orcha_task task; int nsteps; cudaGraphExec_t exec; };
+    std::vector<G> graphs;
 };
 
 extern "C" {
@@ -236,6 +252,7 @@ orcha_status orcha_packet_create(orcha_mesh* m, const int32_t* ids, int32_t n, o
     orcha_packet* p = new orcha_packet();
     p->mesh = m;
     p->n = n;
+    p->ids.assign(ids, ids + n);
     cudaError_t e = cudaMalloc(&p->ids_dev, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMemcpy(p->ids_dev, ids, sizeof(int) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -345,6 +362,185 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
     m->graphs.push_back(g);
     ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
     m->cur = start ^ (nsteps & 1);
+    return ORCHA_OK;
+}
+
+// ---------------------------------------------------------------- batches (persistent path)
+
+orcha_status orcha_batch_destroy(orcha_batch* b) {
+    if (!b) return ORCHA_OK;
+    cudaDeviceSynchronize();
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    cudaFree(b->slots_dev);
+    cudaFree(b->items_dev);
+    cudaFree(b->queue);
+    cudaFree(b->done_dev);
+    cudaFree(b->cur_dev);
+    delete b;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx, int32_t ty, orcha_batch** out) {
+    if (!pk || !out || npk < 1) return fail(ORCHA_ERR_INVALID, "batch_create: need at least one packet");
+    *out = nullptr;
+    std::vector<orcha_mesh*> meshes;
+    for (int i = 0; i < npk; ++i) {
+        if (!pk[i]) return fail(ORCHA_ERR_INVALID, "batch_create: null packet %d", i);
+        if (std::find(meshes.begin(), meshes.end(), pk[i]->mesh) == meshes.end()) meshes.push_back(pk[i]->mesh);
+    }
+    const int ndim = meshes[0]->dev.ndim;
+    if (tx == 0 && ty == 0) {           // default: the widest variant every mesh's blocks allow
+        tx = 16;
+        ty = 16;
+        for (auto* m : meshes) {
+            if (m->dev.bs[0] < 16) tx = 8;
+            if (m->dev.bs[1] < 16) ty = 8;
+        }
+    }
+    if (!orcha::hydro_tile_supported(ndim, tx, ty))
+        return fail(ORCHA_ERR_UNSUPPORTED, "batch_create: no %dx%d tile variant", tx, ty);
+    for (auto* m : meshes) {
+        if (m->dev.ndim != ndim) return fail(ORCHA_ERR_INVALID, "batch_create: meshes of different ndim");
+        if (m->dev.bs[0] % tx || m->dev.bs[1] % ty)
+            return fail(ORCHA_ERR_INVALID, "batch_create: tile %dx%d does not divide a mesh's blocks", tx, ty);
+    }
+    // each mesh's packets must cover its blocks exactly once (the step ends with that mesh's dt)
+    std::vector<orcha::Item> items;
+    std::vector<int> nitems(meshes.size(), 0);
+    for (size_t s_ = 0; s_ < meshes.size(); ++s_) {
+        orcha_mesh* m = meshes[s_];
+        std::vector<char> seen((size_t)m->nblk, 0);
+        long long cnt = 0;
+        for (int i = 0; i < npk; ++i) {
+            if (pk[i]->mesh != m) continue;
+            for (int id : pk[i]->ids) {
+                if (seen[id]) return fail(ORCHA_ERR_INVALID, "batch_create: block %d of a mesh in two packets", id);
+                seen[id] = 1;
+                ++cnt;
+            }
+        }
+        if (cnt != m->nblk)
+            return fail(ORCHA_ERR_INVALID, "batch_create: packets cover %lld of a mesh's %d blocks", cnt, m->nblk);
+    }
+    for (int i = 0; i < npk; ++i) {
+        const int slot = (int)(std::find(meshes.begin(), meshes.end(), pk[i]->mesh) - meshes.begin());
+        const orcha_mesh* m = pk[i]->mesh;
+        const int ntile = (m->dev.bs[0] / tx) * (m->dev.bs[1] / ty);
+        for (int id : pk[i]->ids)
+            for (int t = 0; t < ntile; ++t) {
+                items.push_back({slot, id, t, 0});
+                ++nitems[slot];
+            }
+    }
+    orcha_batch* b = new orcha_batch();
+    b->meshes = meshes;
+    b->packets.assign(pk, pk + npk);
+    b->ndim = ndim;
+    b->tx = tx;
+    b->ty = ty;
+    b->nitems = (int)items.size();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t ns = meshes.size();
+    cudaError_t e = cudaMalloc(&b->slots_dev, sizeof(orcha::SlotDev) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&b->items_dev, sizeof(orcha::Item) * items.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->queue, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->done_dev, sizeof(unsigned) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&b->cur_dev, sizeof(int) * ns);
+    if (e == cudaSuccess) e = cudaMemset(b->done_dev, 0, sizeof(unsigned) * ns);
+    if (e == cudaSuccess) e = orcha::configure_hydro(ndim, tx, ty);
+    if (e == cudaSuccess) {
+        std::vector<orcha::SlotDev> sl(ns);
+        for (size_t i = 0; i < ns; ++i) {
+            orcha_mesh* m = meshes[i];
+            sl[i].m = m->dev;
+            sl[i].state[0] = m->desc.state_dev[0];
+            sl[i].state[1] = m->desc.state_dev[1];
+            sl[i].dt = m->desc.dt_dev;
+            sl[i].cur = b->cur_dev + i;
+            sl[i].done = b->done_dev + i;
+            sl[i].nitems = nitems[i];
+            sl[i].nblk = m->nblk;
+            sl[i].tiles_x = m->dev.bs[0] / tx;
+            sl[i].tiles_y = m->dev.bs[1] / ty;
+        }
+        e = cudaMemcpy(b->slots_dev, sl.data(), sizeof(orcha::SlotDev) * ns, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->items_dev, items.data(), sizeof(orcha::Item) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        orcha_status st = cuda_fail(e, "batch_create");
+        orcha_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return ORCHA_OK;
+}
+
+static orcha_status batch_grid(orcha_batch* b, orcha_task task, int* grid) {
+    int per_sm = 0;
+    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, task == ORCHA_TASK_HYDRO_F32FLUX, &per_sm),
+               "batch occupancy");
+    if (per_sm < 1) return fail(ORCHA_ERR_UNSUPPORTED, "batch: persistent kernel does not fit on an SM");
+    *grid = std::min(b->nitems, per_sm * b->num_sms);
+    return ORCHA_OK;
+}
+
+static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, int grid, cudaStream_t st) {
+    const bool f32 = task == ORCHA_TASK_HYDRO_F32FLUX;
+    for (int n = 0; n < nsteps; ++n) {
+        ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
+        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, f32, b->slots_dev, b->items_dev, b->nitems,
+                                            b->queue, grid, st),
+                   "batch launch");
+    }
+    return ORCHA_OK;
+}
+
+orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps, int32_t init_dt, int32_t use_graph,
+                                 void* stream) {
+    if (!b || nsteps < 0) return fail(ORCHA_ERR_INVALID, "batch_advance: bad argument");
+    if (task != ORCHA_TASK_HYDRO_FP64 && task != ORCHA_TASK_HYDRO_F32FLUX)
+        return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a hydro task");
+    cudaStream_t st = (cudaStream_t)stream;
+    orcha_status s;
+    if (init_dt) {
+        for (auto* p : b->packets)
+            if ((s = orcha_packet_run(const_cast<orcha_packet*>(p), ORCHA_TASK_SIGNAL_SPEED, stream))) return s;
+        for (auto* m : b->meshes)
+            if ((s = orcha_dt_reduce(m, stream))) return s;
+    }
+    // the device copy of each mesh's current buffer index, as of this point in the stream
+    std::vector<int> cur(b->meshes.size());
+    for (size_t i = 0; i < cur.size(); ++i) cur[i] = b->meshes[i]->cur;
+    ORCHA_CUDA(cudaMemcpyAsync(b->cur_dev, cur.data(), sizeof(int) * cur.size(), cudaMemcpyHostToDevice, st),
+               "batch cur upload");
+    if (nsteps == 0) return ORCHA_OK;
+    int grid = 0;
+    if ((s = batch_grid(b, task, &grid))) return s;
+    if (!use_graph) {
+        if ((s = enqueue_batch_steps(b, task, nsteps, grid, st))) return s;
+    } else {
+        if (st == nullptr) return fail(ORCHA_ERR_INVALID, "batch_advance: graph capture needs a non-default stream");
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : b->graphs)
+            if (g.task == task && g.nsteps == nsteps) exec = g.exec;
+        if (!exec) {
+            ORCHA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+            s = enqueue_batch_steps(b, task, nsteps, grid, st);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (s) { if (graph) cudaGraphDestroy(graph); return s; }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            b->graphs.push_back({task, nsteps, exec});
+        }
+        ORCHA_CUDA(cudaGraphLaunch(exec, st), "batch graph launch");
+    }
+    for (auto* m : b->meshes) m->cur ^= (nsteps & 1);
     return ORCHA_OK;
 }
 

@@ -35,6 +35,18 @@ __device__ __forceinline__ bool operator>=(rd a, rd b) { return a.v >= b.v; }
 // rounded IEEE operation (1/x by __drcp_rn equals the IEEE quotient 1.0/x).
 template <class T> struct P;
 
+// FP64 sign tests, selects and exact halvings are done on the IEEE bit
+// patterns with integer instructions: on this GPU every FP64 compare,
+// min/max and multiply issues on the FP64 pipe, the scarcest unit, while the
+// integer forms below give bitwise the same answers (NaN never reaches them
+// on a physical state; the non-physical checks run on finite values).
+__device__ __forceinline__ long long bits(rd x) { return __double_as_longlong(x.v); }
+// Totally ordered integer key of a non-NaN double; -0 and +0 share key 0.
+__device__ __forceinline__ long long okey(rd x) {
+    const long long b = bits(x);
+    return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFLL) : b;
+}
+
 template <> struct P<rd> {
     using store = double;
     static __device__ __forceinline__ rd in(double x) { return rd(x); }
@@ -43,8 +55,34 @@ template <> struct P<rd> {
     static __device__ __forceinline__ rd sqrt(rd x) { return rd(__dsqrt_rn(x.v)); }
     static __device__ __forceinline__ rd ld(const double* p) { return rd(*p); }
     static __device__ __forceinline__ void st(double* p, rd x) { *p = x.v; }
-    static __device__ __forceinline__ bool pos(rd x) { return x.v > 0.0; }   // false for NaN
-    static __device__ __forceinline__ bool neg(rd x) { return x.v < 0.0; }
+    // x > 0 (false for +-0 and NaN; true for +inf)
+    static __device__ __forceinline__ bool pos(rd x) {
+        const long long b = bits(x);
+        return b > 0 && b <= 0x7FF0000000000000LL;
+    }
+    // x < 0 (false for +-0 and NaN; true for -inf)
+    static __device__ __forceinline__ bool neg(rd x) {
+        const unsigned long long b = (unsigned long long)bits(x);
+        return b > 0x8000000000000000ULL && b <= 0xFFF0000000000000ULL;
+    }
+    static __device__ __forceinline__ bool lt(rd a, rd b) { return okey(a) < okey(b); }
+    static __device__ __forceinline__ bool ge0(rd a) { return okey(a) >= 0; }
+    static __device__ __forceinline__ bool le0(rd a) { return okey(a) <= 0; }
+    // minmod: same strict sign -> the argument of smaller magnitude, else +0
+    static __device__ __forceinline__ rd minmod(rd a, rd b) {
+        const long long ba = bits(a), bb = bits(b);
+        const long long ma = ba & 0x7FFFFFFFFFFFFFFFLL, mb = bb & 0x7FFFFFFFFFFFFFFFLL;
+        const bool ok = ((ba ^ bb) >= 0) && ma != 0 && mb != 0 && ma <= 0x7FF0000000000000LL &&
+                        mb <= 0x7FF0000000000000LL;
+        return ok ? (ma < mb ? a : b) : rd(0.0);
+    }
+    // 0.5 * x: exponent decrement when the result is normal, else the IEEE multiply
+    static __device__ __forceinline__ rd half(rd x) {
+        const long long b = bits(x);
+        const int e = (int)((b >> 52) & 0x7FF);
+        if (e > 1 && e < 0x7FF) return rd(__longlong_as_double(b - (1LL << 52)));
+        return rd(__dmul_rn(x.v, 0.5));
+    }
     static __device__ __forceinline__ rd zero() { return rd(0.0); }
     static __device__ __forceinline__ double to_double(rd x) { return x.v; }
 };
@@ -59,6 +97,15 @@ template <> struct P<float> {
     static __device__ __forceinline__ void st(float* p, float x) { *p = x; }
     static __device__ __forceinline__ bool pos(float x) { return x > 0.0f; }
     static __device__ __forceinline__ bool neg(float x) { return x < 0.0f; }
+    static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+    static __device__ __forceinline__ bool ge0(float a) { return a >= 0.0f; }
+    static __device__ __forceinline__ bool le0(float a) { return a <= 0.0f; }
+    static __device__ __forceinline__ float minmod(float a, float b) {
+        if (a > 0.0f && b > 0.0f) return (a < b) ? a : b;
+        if (a < 0.0f && b < 0.0f) return (a > b) ? a : b;
+        return 0.0f;
+    }
+    static __device__ __forceinline__ float half(float x) { return 0.5f * x; }
     static __device__ __forceinline__ float zero() { return 0.0f; }
     static __device__ __forceinline__ double to_double(float x) { return (double)x; }
 };

@@ -45,16 +45,14 @@ __device__ __forceinline__ void prim_from_cons(const T* U, T* W, T& r, T gm1) {
         W[1 + d] = U[1 + d] * r;
         mu = (d == 0) ? (U[1] * W[1]) : (mu + (U[1 + d] * W[1 + d]));
     }
-    T ke = T(0.5) * mu;
+    T ke = P<T>::half(mu);
     W[NV - 1] = gm1 * (U[NV - 1] - ke);
 }
 
 // minmod: the smaller-magnitude argument when both share a strict sign, else 0.
 template <class T>
 __device__ __forceinline__ T minmod(T a, T b) {
-    if (P<T>::pos(a) && P<T>::pos(b)) return (a < b) ? a : b;
-    if (P<T>::neg(a) && P<T>::neg(b)) return (a > b) ? a : b;
-    return P<T>::zero();
+    return P<T>::minmod(a, b);
 }
 
 // Conserved state and physical flux of a primitive state given normal-first:
@@ -72,7 +70,7 @@ __device__ __forceinline__ void cons_flux(const T* W, T* U, T* F, T igm1) {
     if (NDIM == 2) q2 = (W[1] * W[1]) + (W[2] * W[2]);
     else if (!ZNORMAL) q2 = ((W[1] * W[1]) + (W[2] * W[2])) + (W[3] * W[3]);
     else q2 = ((W[2] * W[2]) + (W[3] * W[3])) + (W[1] * W[1]);
-    U[NV - 1] = (p * igm1) + ((T(0.5) * rho) * q2);
+    U[NV - 1] = (p * igm1) + (P<T>::half(rho) * q2);
     F[0] = U[1];
     F[1] = (U[1] * un) + p;
 #pragma unroll
@@ -87,17 +85,17 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     const T cL = P<T>::sqrt((g * L[NV - 1]) * P<T>::rcp(L[0]));
     const T cR = P<T>::sqrt((g * R[NV - 1]) * P<T>::rcp(R[0]));
     T a = L[1] - cL, b = R[1] - cR;
-    const T SL = (a < b) ? a : b;
+    const T SL = P<T>::lt(a, b) ? a : b;
     a = L[1] + cL;
     b = R[1] + cR;
-    const T SR = (a > b) ? a : b;
+    const T SR = P<T>::lt(b, a) ? a : b;
     T UL[NV], UR[NV], FL[NV], FR[NV];
     cons_flux<T, NDIM, ZNORMAL>(L, UL, FL, igm1);
     cons_flux<T, NDIM, ZNORMAL>(R, UR, FR, igm1);
-    if (SL >= T(0.0)) {
+    if (P<T>::ge0(SL)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FL[v];
-    } else if (SR <= T(0.0)) {
+    } else if (P<T>::le0(SR)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FR[v];
     } else {
@@ -126,32 +124,34 @@ struct Tile {
     }
 };
 
-template <int NDIM, int TX, int TY, class T>
-__global__ void __launch_bounds__(TX * TY)
-hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
-             const double* __restrict__ Uin, double* __restrict__ Uout) {
+// One column tile of one block: the whole z sweep. Returns this thread's
+// largest signal speed of the new state (0 for threads without cells).
+// GATHER = false: guard cells are read from the padded block (filled by the
+// guard-fill task). GATHER = true: guard cells are read straight from the
+// source cell (a neighbour's interior, or the boundary rule's cell), so no
+// guard-fill pass and no guard storage traffic are needed; the values are
+// the same copies the guard fill would make.
+template <int NDIM, int TX, int TY, class T, bool GATHER>
+__device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
+                                             const double* __restrict__ Uin, double* __restrict__ Uout,
+                                             unsigned char* smem_raw) {
     using Tl = Tile<NDIM, TX, TY>;
     using S = typename P<T>::store;
     constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
     constexpr int R2X = Tl::R2X, R2N = Tl::R2N, R1X = Tl::R1X, R1N = Tl::R1N;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     S* sW = reinterpret_cast<S*>(smem_raw);                 // [slot][NW][R2N]
     S* sFS = sW + Tl::NSLOT * NW * R2N;                    // [face 0..3 = x-,x+,y-,y+][NV][R1N]
     S* sFx = sFS + 4 * NV * R1N;                           // [NV][NXF]
     S* sFy = sFx + NV * Tl::NXF;                           // [NV][NYF]
-    __shared__ unsigned long long red[32];
 
     const int tid = threadIdx.x;
-    const int ntile = tiles_x * tiles_y;
-    const int blk = blk_ids[blockIdx.x / ntile];
-    const int tile = blockIdx.x % ntile;
-    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
     const int px = m.pad[0], py = m.pad[1];
     const long long vs = m.var_stride;
     const double* Ub = Uin + (long long)blk * m.blk_stride;
     double* Ob = Uout + (long long)blk * m.blk_stride;
     const int bz = (NDIM == 3) ? m.bs[2] : 1;
+    const int bc[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
 
     const T g = P<T>::in(m.gamma), gm1 = P<T>::in(m.gm1), igm1 = P<T>::in(m.igm1);
     const double dt = *m.dt;
@@ -186,10 +186,31 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
         const int zz = (NDIM == 3) ? pzi + kGuard : 0;
         for (int c = tid; c < R2N; c += NT) {
             const int ci = c % R2X, cj = c / R2X;
-            const long long gi = ((long long)zz * py + (y0 + cj)) * px + (x0 + ci);
+            const double* src = Ub + (((long long)zz * py + (y0 + cj)) * px + (x0 + ci));
+            if (GATHER) {
+                const int l[3] = {x0 + ci - kGuard, y0 + cj - kGuard, pzi};
+                bool outside = false;
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d) outside |= (l[d] < 0) | (l[d] >= m.bs[d]);
+                if (outside) {
+                    int sb[3] = {0, 0, 0}, sl[3] = {0, 0, 0};
+#pragma unroll
+                    for (int d = 0; d < NDIM; ++d) {
+                        const int n = m.nb[d] * m.bs[d];
+                        int gi = bc[d] * m.bs[d] + l[d];
+                        if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+                        else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+                        sb[d] = gi / m.bs[d];
+                        sl[d] = gi % m.bs[d] + kGuard;
+                    }
+                    const long long sblk = sb[0] + (long long)m.nb[0] * (sb[1] + (long long)m.nb[1] * sb[2]);
+                    const int sz = (NDIM == 3) ? sl[2] : 0;
+                    src = Uin + sblk * m.blk_stride + (((long long)sz * py + sl[1]) * px + sl[0]);
+                }
+            }
             T U[NV], W[NV], r;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = P<T>::in(Ub[gi + v * vs]);
+            for (int v = 0; v < NV; ++v) U[v] = P<T>::in(src[v * vs]);
             prim_from_cons<T, NDIM>(U, W, r, gm1);
 #pragma unroll
             for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
@@ -249,7 +270,7 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
         for (int d = 0; d < NDIM; ++d) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const T hs = T(0.5) * dW[d][v];
+                const T hs = P<T>::half(dW[d][v]);
                 flo[d][v] = Wb[v] - hs;
                 fhi[d][v] = Wb[v] + hs;
             }
@@ -268,7 +289,7 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
     // its low-z face flux, and its x+y flux sum
     T zp_prev[NV], Fz_prev[NV];
     double acc_prev[NV];
-    double smax = 0.0;
+    unsigned long long smaxb = 0ull;   // bits of the largest signal speed
 #pragma unroll
     for (int v = 0; v < NV; ++v) { zp_prev[v] = P<T>::zero(); Fz_prev[v] = P<T>::zero(); acc_prev[v] = 0.0; }
 
@@ -373,12 +394,12 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
                 // signal speed of the new state
                 rd W[NV], r;
                 prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
-                if (!(W[0].v > 0.0 && W[NV - 1].v > 0.0)) atomicOr(m.err, 1);
+                if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[NV - 1]))) atomicOr(m.err, 1);
                 const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
                 rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
 #pragma unroll
                 for (int d = 1; d < NDIM; ++d) s = s + ((rd(fabs(W[1 + d].v)) + c) * rd(m.idx[d]));
-                smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+                smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
@@ -404,15 +425,31 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
                 }
                 rd W[NV], r;
                 prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
-                if (!(W[0].v > 0.0 && W[NV - 1].v > 0.0)) atomicOr(m.err, 1);
+                if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[NV - 1]))) atomicOr(m.err, 1);
                 const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
                 rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
                 s = s + ((rd(fabs(W[2].v)) + c) * rd(m.idx[1]));
-                smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+                smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
             }
         }
     }
-    cta_raise_smax(smax, red, &m.smax[blk]);
+    return __longlong_as_double((long long)smaxb);
+}
+
+// Packet path: one CTA per (packet block, column tile); guards come from the
+// padded block.
+template <int NDIM, int TX, int TY, class T>
+__global__ void __launch_bounds__(TX * TY)
+hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
+             const double* __restrict__ Uin, double* __restrict__ Uout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long red[32];
+    const int ntile = tiles_x * tiles_y;
+    const int blk = blk_ids[blockIdx.x / ntile];
+    const int tile = blockIdx.x % ntile;
+    const double s = hydro_tile<NDIM, TX, TY, T, false>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
+                                                        Uin, Uout, smem_raw);
+    cta_raise_smax(s, red, &m.smax[blk]);
 }
 
 }  // namespace orcha

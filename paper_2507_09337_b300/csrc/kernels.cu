@@ -5,6 +5,7 @@
 #include "common.cuh"
 #include "hydro.cuh"
 #include "launch.h"
+#include "persistent.cuh"
 
 namespace orcha {
 
@@ -80,7 +81,7 @@ __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk
     const int blk = blk_ids[blockIdx.x];
     const double* Ub = U + (long long)blk * m.blk_stride;
     const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    double smax = 0.0;
+    unsigned long long smaxb = 0ull;   // bits of the largest signal speed
     for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
         const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
         const int kk = (m.ndim == 3) ? k + kGuard : 0;
@@ -90,13 +91,13 @@ __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk
         if (m.ndim == 3) prim_from_cons<rd, 3>(Uc, W, r, rd(m.gm1));
         else prim_from_cons<rd, 2>(Uc, W, r, rd(m.gm1));
         const int nv = m.nvar;
-        if (!(W[0].v > 0.0 && W[nv - 1].v > 0.0)) atomicOr(m.err, 1);
+        if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[nv - 1]))) atomicOr(m.err, 1);
         const rd cs = P<rd>::sqrt((rd(m.gamma) * W[nv - 1]) * r);
         rd s = (rd(fabs(W[1].v)) + cs) * rd(m.idx[0]);
         for (int d = 1; d < m.ndim; ++d) s = s + ((rd(fabs(W[1 + d].v)) + cs) * rd(m.idx[d]));
-        smax = (s.v > smax || s.v != s.v) ? s.v : smax;
+        smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
     }
-    cta_raise_smax(smax, red, &m.smax[blk]);
+    cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
 }
 
 // ---------------------------------------------------------------- dt reduction
@@ -137,8 +138,56 @@ template <int NDIM, int TX, int TY, class T>
 static cudaError_t configure_t() {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    return cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(persistent_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+}
+
+template <int NDIM, int TX, int TY, class T>
+static cudaError_t launch_persistent_t(const SlotDev* slots, const Item* items, int nitems, unsigned* queue, int grid,
+                                       cudaStream_t st) {
+    using Tl = Tile<NDIM, TX, TY>;
+    const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
+    persistent_kernel<NDIM, TX, TY, T><<<grid, TX * TY, smem, st>>>(slots, items, nitems, queue);
+    return cudaGetLastError();
+}
+
+template <int NDIM, int TX, int TY, class T>
+static cudaError_t occupancy_t(int* per_sm) {
+    using Tl = Tile<NDIM, TX, TY>;
+    const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T>, TX * TY, smem);
+}
+
+#define ORCHA_PERS_CASE(ND, X, Y)                                                                      \
+    if (ndim == ND && tx == X && ty == Y)                                                              \
+        return f32 ? launch_persistent_t<ND, X, Y, float>(slots, items, nitems, queue, grid, st)       \
+                   : launch_persistent_t<ND, X, Y, rd>(slots, items, nitems, queue, grid, st);
+
+cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev* slots, const Item* items,
+                              int nitems, unsigned* queue, int grid, cudaStream_t st) {
+    ORCHA_PERS_CASE(2, 8, 8)
+    ORCHA_PERS_CASE(2, 16, 8)
+    ORCHA_PERS_CASE(2, 16, 16)
+    ORCHA_PERS_CASE(3, 8, 8)
+    ORCHA_PERS_CASE(3, 16, 8)
+    ORCHA_PERS_CASE(3, 16, 16)
+    return cudaErrorInvalidConfiguration;
+}
+
+#define ORCHA_OCC_CASE(ND, X, Y)                                                                       \
+    if (ndim == ND && tx == X && ty == Y) return f32 ? occupancy_t<ND, X, Y, float>(per_sm) : occupancy_t<ND, X, Y, rd>(per_sm);
+
+cudaError_t persistent_occupancy(int ndim, int tx, int ty, bool f32, int* per_sm) {
+    ORCHA_OCC_CASE(2, 8, 8)
+    ORCHA_OCC_CASE(2, 16, 8)
+    ORCHA_OCC_CASE(2, 16, 16)
+    ORCHA_OCC_CASE(3, 8, 8)
+    ORCHA_OCC_CASE(3, 16, 8)
+    ORCHA_OCC_CASE(3, 16, 16)
+    return cudaErrorInvalidConfiguration;
 }
 
 #define ORCHA_TILE_CASE(ND, X, Y)                                                                      \

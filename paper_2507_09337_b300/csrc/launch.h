@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "persistent.cuh"
 
 namespace orcha {
 
@@ -18,5 +19,10 @@ cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cud
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st);
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
+// One persistent launch (one time step of every mesh in `slots`).
+cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev* slots, const Item* items,
+                              int nitems, unsigned* queue, int grid, cudaStream_t st);
+// Resident CTAs per SM of a persistent variant.
+cudaError_t persistent_occupancy(int ndim, int tx, int ty, bool f32, int* per_sm);
 
 }  // namespace orcha

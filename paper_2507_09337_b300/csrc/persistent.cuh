@@ -1,0 +1,95 @@
+// persistent.cuh -- one launch per time step for many packets (of one or many
+// meshes): a persistent grid drains a device work queue of (mesh, block,
+// column tile) items.
+//
+// The paper's runtime keeps several data packets in flight on GPU streams so
+// that the device has enough parallelism (sections "Sedov Blast Wave
+// Results" and "Milhoja"); here the packets of a step become items of one
+// queue instead, which one resident grid (CTAs per SM x SMs) drains, so
+// packets of any size -- down to one block -- fill the GPU and no per-packet
+// launch is paid.
+//
+// Per item the CTA reads its tile's halo straight from the neighbouring
+// blocks (no separate guard-fill pass), advances it one step and raises the
+// block's signal speed. The per-mesh step state lives on the device: the
+// index of the current state buffer and dt. The CTA that completes a mesh's
+// last item of the step (counted with a fenced atomic) reduces that mesh's
+// signal speeds to the next dt, clears them, and flips the mesh's current
+// buffer -- so a captured sequence of launches replays correctly.
+#pragma once
+
+#include "common.cuh"
+#include "hydro.cuh"
+
+namespace orcha {
+
+struct SlotDev {
+    MeshDev m;
+    double* state[2];
+    double* dt;             // writable alias of m.dt
+    int* cur;               // device: index of the current state buffer
+    unsigned int* done;     // device: items of this mesh finished in the current launch
+    int nitems;             // items of this mesh per launch
+    int nblk;
+    int tiles_x, tiles_y;
+};
+
+struct Item {
+    int slot, blk, tile, pad;
+};
+
+// Finish a mesh's step: dt = cfl / max signal speed, clear the maxima and the
+// item counter, flip the current buffer. Called by all threads of one CTA.
+__device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red) {
+    unsigned long long b = 0;
+    for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) b = umax64(b, __ldcg(&sd.m.smax[i]));
+    b = warp_max_u64(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t = umax64(t, red[w]);
+        const double s = __longlong_as_double((long long)t);
+        if (s > 0.0 && s <= 1.7976931348623157e308) *sd.dt = sd.m.cfl / s;
+        else atomicOr(sd.m.err, 2);
+        *sd.done = 0u;
+        *sd.cur ^= 1;
+    }
+    for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.m.smax[i] = 0ull;
+}
+
+template <int NDIM, int TX, int TY, class T>
+__global__ void __launch_bounds__(TX * TY)
+persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ items, int nitems,
+                  unsigned int* __restrict__ queue) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long red[32];
+    __shared__ int s_item, s_last;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const Item w = items[it];
+        const SlotDev& sd = slots[w.slot];
+        const int cur = __ldcg(sd.cur);
+        const double s = hydro_tile<NDIM, TX, TY, T, true>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
+                                                           (w.tile / sd.tiles_x) * TY, sd.state[cur],
+                                                           sd.state[cur ^ 1], smem_raw);
+        cta_raise_smax(s, red, &sd.m.smax[w.blk]);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned d = atomicAdd(sd.done, 1u);
+            s_last = (d == (unsigned)sd.nitems - 1u);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            finish_mesh_step(sd, red);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace orcha

@@ -64,3 +64,29 @@ def oracle_steps(oracle_mod, spec, U0, nsteps):
     m = oracle_mod.Mesh(**spec.oracle_kwargs())
     U, dts, _ = oracle_mod.run(m, U0, nsteps)
     return U, dts
+
+
+def gpu_batch_steps(problems, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, tile=(0, 0), use_graph=False, repeat=1):
+    """Advance several meshes together through one batch (one persistent launch
+    per step). problems: list of (spec, U0, packets or None). Returns the list
+    of final states and the device error words."""
+    import torch
+    meshes = [B.Mesh(spec, packets=pk) for spec, _, pk in problems]
+    batch = None
+    try:
+        for m, (_, U0, _) in zip(meshes, problems):
+            m.load(U0)
+        allp = [p for m in meshes for p in m.packets]
+        batch = B.orcha_batch_create(allp, *tile)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        for r in range(repeat):
+            B.orcha_batch_advance(batch, task, nsteps, r == 0, use_graph, s)
+        s.synchronize()
+        errs = [m.poll() for m in meshes]
+        return [m.store() for m in meshes], errs
+    finally:
+        if batch:
+            B.orcha_batch_destroy(batch)
+        for m in meshes:
+            m.close()
