@@ -202,6 +202,32 @@ ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
 ORCHA_API orcha_status orcha_batch_advance(orcha_batch* batch, orcha_task hydro_task, int32_t nsteps,
                                            int32_t init_dt, int32_t use_graph, void* stream);
 
+/* ------------------------------------------------------------------ no-allocation CFL step
+ * The paper has no counterpart to this call. It serves callers that cannot
+ * let a library allocate device memory (for example a host code whose own
+ * allocator owns all of HBM, or a time loop where allocation is forbidden).
+ *
+ * Computes dt_dev = cfl / (largest signal speed sum_d (|u_d| + c) / dx_d over
+ * the interior cells of desc->state_dev[current]) -- the same value that the
+ * SIGNAL_SPEED task followed by orcha_dt_reduce gives -- without creating a
+ * mesh and without any allocation: no cudaMalloc, no cudaFree, no allocating
+ * library routine. Its per-block scratch is a file-scope device array of
+ * ORCHA_NOALLOC_MAX_BLOCKS entries that every GPU loading the library holds
+ * until exit; meshes with more blocks are rejected with ORCHA_ERR_INVALID.
+ * The caller passes the inputs and outputs: desc (geometry, state buffers,
+ * dt_dev) and err_dev, a device int32 into which ORCHA_DEVERR_* bits are
+ * OR-ed (the caller clears it); guards need not be filled.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and clears the entries it uses
+ * at its start, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. Asynchronous on
+ * `stream`. Errors: INVALID (descriptor, buffers, size limit), UNSUPPORTED,
+ * CUDA. */
+#define ORCHA_NOALLOC_MAX_BLOCKS 65536
+ORCHA_API orcha_status orcha_cfl_dt_noalloc(const orcha_mesh_desc* desc, int32_t current, int32_t* err_dev,
+                                            void* stream);
+
 /* Wait for `stream`, then read the device error word into *device_error (0 =
  * none) and clear it. Returns NONFINITE / TIMEOUT when a bit is set. */
 ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* device_error);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "orcha_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "orcha_batch_destroy": (_st, [_vp]),
     "orcha_batch_advance": (_st, [_vp, ctypes.c_int, _i32, _i32, _i32, _vp]),
+    "orcha_cfl_dt_noalloc": (_st, [ctypes.POINTER(orcha_mesh_desc), _i32, _vp, _vp]),
     "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
@@ -197,6 +198,12 @@ def orcha_batch_destroy(batch: int) -> None:
 def orcha_batch_advance(batch: int, task: int, nsteps: int, init_dt: bool, use_graph: bool, stream=None) -> None:
     _check(lib().orcha_batch_advance(batch, int(task), int(nsteps), int(bool(init_dt)), int(bool(use_graph)),
                                      _stream_ptr(stream)))
+
+
+def orcha_cfl_dt_noalloc(desc: orcha_mesh_desc, current: int, err_dev_ptr: int, stream=None) -> None:
+    """dt of desc.state_dev[current] into desc.dt_dev with no device allocation
+    (see include/orcha.h)."""
+    _check(lib().orcha_cfl_dt_noalloc(ctypes.byref(desc), int(current), err_dev_ptr, _stream_ptr(stream)))
 
 
 def orcha_mesh_poll(mesh: int, stream=None) -> int:

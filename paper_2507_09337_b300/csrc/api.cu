@@ -97,32 +97,32 @@ size_t orcha_state_elems(const orcha_mesh_desc* d) {
     return n;
 }
 
-orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
-    if (!d || !out) return fail(ORCHA_ERR_INVALID, "mesh_create: null argument");
-    *out = nullptr;
-    if (d->ndim != 2 && d->ndim != 3) return fail(ORCHA_ERR_INVALID, "mesh_create: ndim must be 2 or 3");
-    for (int a = 0; a < 3; ++a) {
-        if (d->nb[a] < 1) return fail(ORCHA_ERR_INVALID, "mesh_create: nb[%d] < 1", a);
-        if (a < d->ndim && !valid_bs(d->bs[a]))
-            return fail(ORCHA_ERR_INVALID, "mesh_create: bs[%d] = %d (must be 8, 16 or 32)", a, d->bs[a]);
-        if (a >= d->ndim && (d->bs[a] != 1 || d->nb[a] != 1))
-            return fail(ORCHA_ERR_INVALID, "mesh_create: 2D meshes need nb[2] = bs[2] = 1");
-        if (a < d->ndim && !(d->hi[a] > d->lo[a])) return fail(ORCHA_ERR_INVALID, "mesh_create: hi[%d] <= lo[%d]", a, a);
-        if (d->periodic[a] != 0 && d->periodic[a] != 1) return fail(ORCHA_ERR_INVALID, "mesh_create: periodic flag");
-    }
-    if (!(d->gamma > 1.0) || !(d->cfl > 0.0)) return fail(ORCHA_ERR_INVALID, "mesh_create: need gamma > 1, cfl > 0");
-    if (!d->state_dev[0] || !d->state_dev[1] || !d->dt_dev || d->state_dev[0] == d->state_dev[1])
-        return fail(ORCHA_ERR_INVALID, "mesh_create: two distinct state buffers and dt_dev are required");
-    if (((uintptr_t)d->state_dev[0] | (uintptr_t)d->state_dev[1] | (uintptr_t)d->dt_dev) & 7)
-        return fail(ORCHA_ERR_INVALID, "mesh_create: buffers must be 8-byte aligned");
-    const long long nblk = (long long)d->nb[0] * d->nb[1] * d->nb[2];
-    if (nblk > (1LL << 30)) return fail(ORCHA_ERR_INVALID, "mesh_create: too many blocks");
+}  // extern "C"
 
-    orcha_mesh* m = new orcha_mesh();
-    m->desc = *d;
-    m->nblk = (int)nblk;
-    cudaGetDevice(&m->device);
-    MeshDev& v = m->dev;
+namespace orcha {
+
+orcha_status set_error(orcha_status code, const char* msg) { return fail(code, "%s", msg); }
+
+orcha_status cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+// Check a descriptor and fill the kernels' view of it (without the smax and
+// err scratch pointers). Host-only; touches no device state.
+orcha_status mesh_dev_from_desc(const orcha_mesh_desc* d, MeshDev* out, long long* nblk_out) {
+    if (!d || !out) return fail(ORCHA_ERR_INVALID, "null descriptor");
+    if (d->ndim != 2 && d->ndim != 3) return fail(ORCHA_ERR_INVALID, "mesh: ndim must be 2 or 3");
+    for (int a = 0; a < 3; ++a) {
+        if (d->nb[a] < 1) return fail(ORCHA_ERR_INVALID, "mesh: nb[%d] < 1", a);
+        if (a < d->ndim && !valid_bs(d->bs[a]))
+            return fail(ORCHA_ERR_INVALID, "mesh: bs[%d] = %d (must be 8, 16 or 32)", a, d->bs[a]);
+        if (a >= d->ndim && (d->bs[a] != 1 || d->nb[a] != 1))
+            return fail(ORCHA_ERR_INVALID, "mesh: 2D meshes need nb[2] = bs[2] = 1");
+        if (a < d->ndim && !(d->hi[a] > d->lo[a])) return fail(ORCHA_ERR_INVALID, "mesh: hi[%d] <= lo[%d]", a, a);
+        if (d->periodic[a] != 0 && d->periodic[a] != 1) return fail(ORCHA_ERR_INVALID, "mesh: periodic flag");
+    }
+    if (!(d->gamma > 1.0) || !(d->cfl > 0.0)) return fail(ORCHA_ERR_INVALID, "mesh: need gamma > 1, cfl > 0");
+    const long long nblk = (long long)d->nb[0] * d->nb[1] * d->nb[2];
+    if (nblk > (1LL << 30)) return fail(ORCHA_ERR_INVALID, "mesh: too many blocks");
+    MeshDev v{};
     v.ndim = d->ndim;
     v.nvar = d->ndim + 2;
     for (int a = 0; a < 3; ++a) {
@@ -141,6 +141,32 @@ orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
     v.igm1 = 1.0 / (d->gamma - 1.0);
     v.cfl = d->cfl;
     v.dt = d->dt_dev;
+    *out = v;
+    if (nblk_out) *nblk_out = nblk;
+    return ORCHA_OK;
+}
+
+}  // namespace orcha
+
+extern "C" {
+
+orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
+    if (!d || !out) return fail(ORCHA_ERR_INVALID, "mesh_create: null argument");
+    *out = nullptr;
+    MeshDev v;
+    long long nblk = 0;
+    orcha_status st = orcha::mesh_dev_from_desc(d, &v, &nblk);
+    if (st) return st;
+    if (!d->state_dev[0] || !d->state_dev[1] || !d->dt_dev || d->state_dev[0] == d->state_dev[1])
+        return fail(ORCHA_ERR_INVALID, "mesh_create: two distinct state buffers and dt_dev are required");
+    if (((uintptr_t)d->state_dev[0] | (uintptr_t)d->state_dev[1] | (uintptr_t)d->dt_dev) & 7)
+        return fail(ORCHA_ERR_INVALID, "mesh_create: buffers must be 8-byte aligned");
+
+    orcha_mesh* m = new orcha_mesh();
+    m->desc = *d;
+    m->nblk = (int)nblk;
+    cudaGetDevice(&m->device);
+    m->dev = v;
     m->ncell = (long long)d->bs[0] * d->bs[1] * d->bs[2];
 
     cudaError_t e = cudaMalloc(&m->smax, sizeof(unsigned long long) * nblk);
@@ -156,8 +182,8 @@ orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
         orcha_mesh_destroy(m);
         return s;
     }
-    v.smax = m->smax;
-    v.err = m->err;
+    m->dev.smax = m->smax;
+    m->dev.err = m->err;
     *out = m;
     return ORCHA_OK;
 }
@@ -275,6 +301,8 @@ orcha_status orcha_packet_destroy(orcha_packet* p) {
 orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
     if (!p) return fail(ORCHA_ERR_INVALID, "packet_run: null packet");
     orcha_mesh* m = p->mesh;
+    if (!m->dev.smax || !m->dev.err || m->dev.dt != m->desc.dt_dev)
+        return fail(ORCHA_ERR_INVALID, "packet_run: mesh scratch not set up");
     cudaStream_t st = (cudaStream_t)stream;
     double* cur = m->desc.state_dev[m->cur];
     double* nxt = m->desc.state_dev[m->cur ^ 1];
@@ -295,6 +323,7 @@ orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
 
 orcha_status orcha_dt_reduce(orcha_mesh* m, void* stream) {
     if (!m) return fail(ORCHA_ERR_INVALID, "dt_reduce: null mesh");
+    if (!m->dev.smax || !m->dev.err) return fail(ORCHA_ERR_INVALID, "dt_reduce: mesh scratch not set up");
     ORCHA_CUDA(orcha::launch_dt_reduce(m->dev, m->nblk, m->desc.dt_dev, (cudaStream_t)stream), "dt_reduce launch");
     return ORCHA_OK;
 }
@@ -400,6 +429,7 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
     if (!orcha::hydro_tile_supported(ndim, tx, ty))
         return fail(ORCHA_ERR_UNSUPPORTED, "batch_create: no %dx%d tile variant", tx, ty);
     for (auto* m : meshes) {
+        if (!m->dev.smax || !m->dev.err) return fail(ORCHA_ERR_INVALID, "batch_create: mesh scratch not set up");
         if (m->dev.ndim != ndim) return fail(ORCHA_ERR_INVALID, "batch_create: meshes of different ndim");
         if (m->dev.bs[0] % tx || m->dev.bs[1] % ty)
             return fail(ORCHA_ERR_INVALID, "batch_create: tile %dx%d does not divide a mesh's blocks", tx, ty);

@@ -79,25 +79,8 @@ __global__ void unpack_kernel(const MeshDev m, const double* __restrict__ U, dou
 __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk_ids, const double* __restrict__ U) {
     __shared__ unsigned long long red[32];
     const int blk = blk_ids[blockIdx.x];
-    const double* Ub = U + (long long)blk * m.blk_stride;
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    unsigned long long smaxb = 0ull;   // bits of the largest signal speed
-    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
-        const int kk = (m.ndim == 3) ? k + kGuard : 0;
-        const long long po = ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
-        rd Uc[5], W[5], r;
-        for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
-        if (m.ndim == 3) prim_from_cons<rd, 3>(Uc, W, r, rd(m.gm1));
-        else prim_from_cons<rd, 2>(Uc, W, r, rd(m.gm1));
-        const int nv = m.nvar;
-        if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[nv - 1]))) atomicOr(m.err, 1);
-        const rd cs = P<rd>::sqrt((rd(m.gamma) * W[nv - 1]) * r);
-        rd s = (rd(fabs(W[1].v)) + cs) * rd(m.idx[0]);
-        for (int d = 1; d < m.ndim; ++d) s = s + ((rd(fabs(W[1 + d].v)) + cs) * rd(m.idx[d]));
-        smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
-    }
-    cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
+    const unsigned long long b = block_signal_speed(m, blk, U);
+    cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
 }
 
 // ---------------------------------------------------------------- dt reduction

@@ -3,10 +3,18 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/orcha.h"
 #include "common.cuh"
 #include "persistent.cuh"
 
 namespace orcha {
+
+// Error reporting of the C ABI (sets the calling thread's orcha_last_error).
+orcha_status set_error(orcha_status code, const char* msg);
+orcha_status cuda_error(cudaError_t e, const char* what);
+// Validate a descriptor and build the kernels' view of it (scratch pointers
+// left null). Host-only.
+orcha_status mesh_dev_from_desc(const orcha_mesh_desc* d, MeshDev* out, long long* nblk_out);
 
 cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* ids, int n, const double* Uin,
                          double* Uout, cudaStream_t st);
