@@ -39,6 +39,30 @@ BYTES_PER_ZONE_3D = 80        # read U^n and write U^{n+1}: 5 vars x 8 B x 2
 FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 2032 MHz, non-FMA ops
 
 
+KERNEL_SOURCES = ["paper_2507_09337_b300/csrc/common.cuh", "paper_2507_09337_b300/csrc/hydro.cuh",
+                  "paper_2507_09337_b300/csrc/persistent.cuh"]
+
+
+def profiled_traffic(profile_md: str):
+    """DRAM bytes per launch from a committed ncu summary, or None if the
+    kernel sources changed since that capture (hash mismatch)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", profile_md)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("    "):
+            k, v = line.strip().split(":", 1)
+            fields[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if fields.get("kernel_source_sha256") != h.hexdigest():
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,8 +298,9 @@ def main():
     fp64_bound = task_name == "fp64"
     if fp64_bound:
         achieved = FLOPS_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e12
+        traffic = profiled_traffic("persistent_kernel_fp64_sedov128.md") if args.workload == "sedov128" else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "persistent_kernel<3,16,16,rd>", "per_launch": "one time step of all packets",
                 "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
     else:
