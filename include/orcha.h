@@ -202,6 +202,22 @@ ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
 ORCHA_API orcha_status orcha_batch_advance(orcha_batch* batch, orcha_task hydro_task, int32_t nsteps,
                                            int32_t init_dt, int32_t use_graph, void* stream);
 
+/* ------------------------------------------------------------------ autotuning
+ * Pick the fastest built column tile (tx, ty) of the hydro kernel for blocks
+ * of bs[0] x bs[1] (x bs[2] in 3D) cells and the given hydro task: each
+ * variant dividing the block is timed on a synthetic periodic mesh of about
+ * `nblocks` blocks through the persistent batch path (2 warm-up + 5 timed
+ * steps). All variants give the same result bits; the choice only affects
+ * speed. With cache_path != NULL the answer is read from / written to that
+ * JSON file, keyed by GPU name, ndim, block size and task, so tuning runs once
+ * per machine. ms_out (may be NULL) receives the best time per step (-1 when a
+ * cache entry has none). Allocates and frees its own temporary mesh;
+ * synchronises the device. The paper names auto-tuned kernel generation as
+ * future work (section "Conclusions"). Errors: INVALID, UNSUPPORTED, OOM,
+ * CUDA. */
+ORCHA_API orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_task hydro_task, int32_t nblocks,
+                                      const char* cache_path, int32_t* tx, int32_t* ty, double* ms_out);
+
 /* ------------------------------------------------------------------ no-allocation CFL step
  * The paper has no counterpart to this call. It serves callers that cannot
  * let a library allocate device memory (for example a host code whose own

@@ -82,6 +82,8 @@ SIGNATURES = {
     "orcha_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "orcha_batch_destroy": (_st, [_vp]),
     "orcha_batch_advance": (_st, [_vp, ctypes.c_int, _i32, _i32, _i32, _vp]),
+    "orcha_autotune": (_st, [_i32, ctypes.POINTER(_i32), ctypes.c_int, _i32, ctypes.c_char_p, ctypes.POINTER(_i32),
+                             ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
     "orcha_cfl_dt_noalloc": (_st, [ctypes.POINTER(orcha_mesh_desc), _i32, _vp, _vp]),
     "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
     "orcha_last_error": (ctypes.c_char_p, []),
@@ -198,6 +200,21 @@ def orcha_batch_destroy(batch: int) -> None:
 def orcha_batch_advance(batch: int, task: int, nsteps: int, init_dt: bool, use_graph: bool, stream=None) -> None:
     _check(lib().orcha_batch_advance(batch, int(task), int(nsteps), int(bool(init_dt)), int(bool(use_graph)),
                                      _stream_ptr(stream)))
+
+
+DEFAULT_TUNE_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "orcha_b300", "tiles.json")
+
+
+def orcha_autotune(ndim: int, bs, task: int, nblocks: int = 296, cache_path: str | None = DEFAULT_TUNE_CACHE):
+    """Fastest (tx, ty, ms_per_step) tile for this block geometry and task."""
+    if cache_path:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+    b = (_i32 * 3)(*[int(x) for x in bs])
+    tx, ty, ms = _i32(), _i32(), ctypes.c_double()
+    _check(lib().orcha_autotune(int(ndim), b, int(task), int(nblocks),
+                                cache_path.encode() if cache_path else None,
+                                ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(ms)))
+    return tx.value, ty.value, ms.value
 
 
 def orcha_cfl_dt_noalloc(desc: orcha_mesh_desc, current: int, err_dev_ptr: int, stream=None) -> None:

@@ -40,50 +40,11 @@ orcha_status cuda_fail(cudaError_t e, const char* what) {
 
 bool valid_bs(int b) { return b == 8 || b == 16 || b == 32; }
 
-struct GraphEntry {
-    std::vector<const orcha_packet*> packets;
-    orcha_task task;
-    int nsteps, init_dt, start_cur;
-    cudaGraphExec_t exec;
-};
+
 
 }  // namespace
 
-struct orcha_mesh {
-    orcha_mesh_desc desc;
-    MeshDev dev;
-    int cur = 0;
-    int nblk = 0;
-    long long ncell = 0;             // interior cells per block
-    unsigned long long* smax = nullptr;
-    int* err = nullptr;
-    double* staging = nullptr;       // device staging of interior arrays for host load/store
-    int tile_x = 8, tile_y = 8;
-    int device = 0;
-    std::vector<GraphEntry> graphs;
-};
-
-struct orcha_packet {
-    orcha_mesh* mesh;
-    int n;
-    int* ids_dev;
-    std::vector<int> ids;
-};
-
-struct orcha_batch {
-    std::vector<orcha_mesh*> meshes;                 // one slot per mesh
-    std::vector<const orcha_packet*> packets;
-    int ndim = 3, tx = 8, ty = 8;
-    int nitems = 0;
-    orcha::SlotDev* slots_dev = nullptr;
-    orcha::Item* items_dev = nullptr;
-    unsigned* queue = nullptr;
-    unsigned* done_dev = nullptr;
-    int* cur_dev = nullptr;
-    int num_sms = 0;
-    struct G { orcha_task task; int nsteps; cudaGraphExec_t exec; };
-    std::vector<G> graphs;
-};
+#include "runtime.h"
 
 extern "C" {
 
@@ -379,7 +340,7 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
     m->cur = start;
     if (s) { if (graph) cudaGraphDestroy(graph); return s; }
     if (e != cudaSuccess) return cuda_fail(e, "end capture");
-    GraphEntry g;
+    orcha::GraphEntry g;
     g.packets.assign(pk, pk + npk);
     g.task = task;
     g.nsteps = nsteps;

@@ -105,6 +105,40 @@ __global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) m.smax[i] = 0ull;
 }
 
+// ---------------------------------------------------------------- synthetic state (autotuning)
+// A smooth, everywhere-physical state computed from the cell position alone:
+// rho = 1 + 0.2 sin(2 pi (x + 2y + 3z)), u_d = 0.3 cos(2 pi (d + 1) x_d), p = 1 + 0.1 cos(...).
+__global__ void synthetic_state_kernel(const MeshDev m, double* __restrict__ U) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long blk = e / ncell, c = e % ncell;
+        const int l[3] = {(int)(c % m.bs[0]), (int)((c / m.bs[0]) % m.bs[1]), (int)(c / ((long long)m.bs[0] * m.bs[1]))};
+        const int b[3] = {(int)(blk % m.nb[0]), (int)((blk / m.nb[0]) % m.nb[1]), (int)(blk / ((long long)m.nb[0] * m.nb[1]))};
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = (b[d] * m.bs[d] + l[d] + 0.5) / (double)(m.nb[d] * m.bs[d]);
+        const double ph = 6.283185307179586 * (x[0] + 2.0 * x[1] + (m.ndim == 3 ? 3.0 * x[2] : 0.0));
+        const double rho = 1.0 + 0.2 * sin(ph), p = 1.0 + 0.1 * cos(ph);
+        double ke = 0.0, mom[3];
+        for (int d = 0; d < m.ndim; ++d) {
+            const double u = 0.3 * cos(6.283185307179586 * (d + 1) * x[d]);
+            mom[d] = rho * u;
+            ke += 0.5 * rho * u * u;
+        }
+        const int kk = (m.ndim == 3) ? l[2] + kGuard : 0;
+        const long long po = blk * m.blk_stride + ((long long)kk * m.pad[1] + (l[1] + kGuard)) * m.pad[0] + (l[0] + kGuard);
+        U[po] = rho;
+        for (int d = 0; d < m.ndim; ++d) U[po + (1 + d) * m.var_stride] = mom[d];
+        U[po + (m.nvar - 1) * m.var_stride] = p * m.igm1 + ke;
+    }
+}
+
+cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st) {
+    synthetic_state_kernel<<<148 * 8, 256, 0, st>>>(m, U);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- hydro launch table
 template <int NDIM, int TX, int TY, class T>
 static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,

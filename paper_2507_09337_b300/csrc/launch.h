@@ -27,6 +27,10 @@ cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cud
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st);
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
+// Fill the interiors of a padded state with a smooth physical state (autotuning input).
+cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st);
+// Built column-tile variants, widest first.
+constexpr int kTiles[3][2] = {{16, 16}, {16, 8}, {8, 8}};
 // One persistent launch (one time step of every mesh in `slots`).
 cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev* slots, const Item* items,
                               int nitems, unsigned* queue, int grid, cudaStream_t st);

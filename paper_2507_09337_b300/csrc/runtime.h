@@ -1,0 +1,57 @@
+// runtime.h -- host-side runtime objects behind the opaque C-ABI handles
+// (internal to the library).
+#pragma once
+
+#include <vector>
+
+#include "../../include/orcha.h"
+#include "common.cuh"
+#include "persistent.cuh"
+
+namespace orcha {
+
+// A captured multi-step sequence of one mesh (orcha_mesh_advance).
+struct GraphEntry {
+    std::vector<const orcha_packet*> packets;
+    orcha_task task;
+    int nsteps, init_dt, start_cur;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace orcha
+
+struct orcha_mesh {
+    orcha_mesh_desc desc;
+    orcha::MeshDev dev;
+    int cur = 0;
+    int nblk = 0;
+    long long ncell = 0;             // interior cells per block
+    unsigned long long* smax = nullptr;
+    int* err = nullptr;
+    double* staging = nullptr;       // device staging of interior arrays for host load/store
+    int tile_x = 8, tile_y = 8;
+    int device = 0;
+    std::vector<orcha::GraphEntry> graphs;
+};
+
+struct orcha_packet {
+    orcha_mesh* mesh;
+    int n;
+    int* ids_dev;
+    std::vector<int> ids;
+};
+
+struct orcha_batch {
+    std::vector<orcha_mesh*> meshes;                 // one slot per mesh
+    std::vector<const orcha_packet*> packets;
+    int ndim = 3, tx = 8, ty = 8;
+    int nitems = 0;
+    orcha::SlotDev* slots_dev = nullptr;
+    orcha::Item* items_dev = nullptr;
+    unsigned* queue = nullptr;
+    unsigned* done_dev = nullptr;
+    int* cur_dev = nullptr;
+    int num_sms = 0;
+    struct G { orcha_task task; int nsteps; cudaGraphExec_t exec; };
+    std::vector<G> graphs;
+};
