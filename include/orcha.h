@@ -66,6 +66,18 @@ typedef int32_t orcha_status;
 #define ORCHA_DEVERR_BAD_DT 2      /* the reduced signal speed was not positive and finite */
 #define ORCHA_DEVERR_TIMEOUT 4     /* a device-side bounded wait gave up */
 
+/* Initial states (orcha_mesh_init_region, serving requests). FROM_HOST copies
+ * host data in. The two
+ * recipes write the initial state on the device (no host transfer): cell g
+ * (global index per axis) is inside the region when, in half-cell units
+ * (cell centre at 2g + 1), sum_d (2 g_d + 1 - region[d])^2 <= region[3]
+ * (SPHERE), or when g[region[0]] < region[1] (HALF_SPACE); inside cells take
+ * the conserved state u_in, the others u_out (Sedov-like and Sod-like
+ * problems). */
+#define ORCHA_INIT_FROM_HOST 0
+#define ORCHA_INIT_SPHERE 1
+#define ORCHA_INIT_HALF_SPACE 2
+
 /* Tasks a packet can run (orcha_packet_run). */
 typedef enum {
     /* Refresh the two guard layers of every packet block in the current
@@ -147,6 +159,12 @@ ORCHA_API orcha_status orcha_mesh_load(orcha_mesh* mesh, const double* interior,
  * (same layout and host_ptr meaning as orcha_mesh_load). */
 ORCHA_API orcha_status orcha_mesh_store(orcha_mesh* mesh, double* interior, int32_t host_ptr, void* stream);
 
+/* Write a two-region initial state (ORCHA_INIT_SPHERE or ORCHA_INIT_HALF_SPACE,
+ * rule as for serving requests below) into the interiors of the current
+ * state buffer on the device. Errors: INVALID, CUDA. */
+ORCHA_API orcha_status orcha_mesh_init_region(orcha_mesh* mesh, int32_t kind, const int32_t region[4],
+                                              const double u_in[5], const double u_out[5], void* stream);
+
 /* Create a packet over n distinct block ids of the mesh (host array, copied).
  * Errors: INVALID (n < 1, an id outside [0, nblocks) or repeated), OOM, CUDA. */
 ORCHA_API orcha_status orcha_packet_create(orcha_mesh* mesh, const int32_t* block_ids, int32_t n, orcha_packet** out);
@@ -201,6 +219,67 @@ ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
  * mesh's current buffer is the one its last step wrote. */
 ORCHA_API orcha_status orcha_batch_advance(orcha_batch* batch, orcha_task hydro_task, int32_t nsteps,
                                            int32_t init_dt, int32_t use_graph, void* stream);
+
+/* ------------------------------------------------------------------ serving
+ * A server advances independent simulations ("requests") with continuous
+ * batching. The paper's runtime keeps data packets moving between host and
+ * device on GPU streams so transfers hide behind computation (sections
+ * "Milhoja" and "Sedov Blast Wave Results"); here one worker thread owns the
+ * device: it admits requests in arrival order while their state fits an
+ * HBM budget (one device pool reserved at creation; a request that does not
+ * fit waits, it is not failed), copies their initial state in on a copy
+ * stream, advances every admitted request by one time step per persistent
+ * launch (requests join and leave between launches; at most two launches
+ * are queued ahead), and copies finished requests out on the copy stream.
+ * Each request keeps its own dt. A request's result does not depend on the
+ * other requests in flight. */
+typedef struct orcha_server orcha_server;
+
+
+typedef struct orcha_request_desc {
+    int32_t ndim, nb[3], bs[3], periodic[3]; /* as in orcha_mesh_desc */
+    double gamma, cfl, lo[3], hi[3];
+    int32_t nsteps;           /* time steps to advance (>= 1); the first dt comes from the initial state */
+    int32_t task;             /* ORCHA_TASK_HYDRO_FP64 or ORCHA_TASK_HYDRO_F32FLUX */
+    int32_t init_kind;        /* ORCHA_INIT_* */
+    int32_t region[4];
+    double u_in[5], u_out[5]; /* conserved states (rho, m_x, m_y[, m_z], E) of the recipes */
+    const double* init_host;  /* FROM_HOST: interior cells [block][var][k][j][i]; host memory (pinned
+                                 for overlap) valid until the request completes */
+    double* out_host;         /* NULL, or the same layout: receives the final state */
+} orcha_request_desc;
+
+typedef struct orcha_request_stats {
+    double t_submit_us, t_admit_us, t_ready_us, t_done_us; /* server clock (us since creation) */
+    int64_t zone_updates;     /* interior cells x steps */
+    double totals[5];         /* final sum over interior cells of each conserved variable (fixed order) */
+    double dt_next;           /* the time step the final state gives */
+    int32_t device_error;     /* ORCHA_DEVERR_* bits this request raised */
+    int32_t status;           /* ORCHA_OK, or ORCHA_ERR_NONFINITE when device_error != 0 */
+} orcha_request_stats;
+
+typedef struct orcha_server_stats {
+    int64_t submitted, completed, steps_launched, zone_updates;
+    double now_us;
+    size_t pool_bytes, pool_peak_bytes;
+} orcha_server_stats;
+
+/* Reserve a device pool of hbm_budget_bytes and start the worker on the
+ * current device. max_active bounds the requests holding device memory at
+ * once. Errors: INVALID, OOM, CUDA. */
+ORCHA_API orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, orcha_server** out);
+/* Stop the worker, wait for the device, free everything. Requests not yet
+ * waited for are dropped. */
+ORCHA_API orcha_status orcha_server_destroy(orcha_server* server);
+/* Queue a request (thread-safe, returns at once). Errors: INVALID
+ * (geometry, steps, task, buffers), OOM (larger than the whole budget). */
+ORCHA_API orcha_status orcha_server_submit(orcha_server* server, const orcha_request_desc* request, int64_t* ticket);
+/* Block until the request is done (timeout_ms < 0: no limit) and release its
+ * ticket; stats may be NULL. Errors: TIMEOUT (still running, ticket kept),
+ * NONFINITE (finished with a device error), INVALID, CUDA (server failed). */
+ORCHA_API orcha_status orcha_server_wait(orcha_server* server, int64_t ticket, int32_t timeout_ms,
+                                         orcha_request_stats* stats);
+ORCHA_API orcha_status orcha_server_get_stats(orcha_server* server, orcha_server_stats* out);
 
 /* ------------------------------------------------------------------ autotuning
  * Pick the fastest built column tile (tx, ty) of the hydro kernel for blocks

@@ -34,6 +34,10 @@ ORCHA_TASK_HYDRO_FP64 = 1
 ORCHA_TASK_HYDRO_F32FLUX = 2
 ORCHA_TASK_SIGNAL_SPEED = 3
 
+ORCHA_INIT_FROM_HOST = 0
+ORCHA_INIT_SPHERE = 1
+ORCHA_INIT_HALF_SPACE = 2
+
 TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX}
 
 
@@ -58,6 +62,33 @@ class orcha_mesh_desc(ctypes.Structure):
     ]
 
 
+class orcha_request_desc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32), ("nb", ctypes.c_int32 * 3), ("bs", ctypes.c_int32 * 3),
+        ("periodic", ctypes.c_int32 * 3), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("nsteps", ctypes.c_int32),
+        ("task", ctypes.c_int32), ("init_kind", ctypes.c_int32), ("region", ctypes.c_int32 * 4),
+        ("u_in", ctypes.c_double * 5), ("u_out", ctypes.c_double * 5),
+        ("init_host", ctypes.c_void_p), ("out_host", ctypes.c_void_p),
+    ]
+
+
+class orcha_request_stats(ctypes.Structure):
+    _fields_ = [
+        ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_ready_us", ctypes.c_double),
+        ("t_done_us", ctypes.c_double), ("zone_updates", ctypes.c_int64), ("totals", ctypes.c_double * 5),
+        ("dt_next", ctypes.c_double), ("device_error", ctypes.c_int32), ("status", ctypes.c_int32),
+    ]
+
+
+class orcha_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("steps_launched", ctypes.c_int64),
+        ("zone_updates", ctypes.c_int64), ("now_us", ctypes.c_double), ("pool_bytes", ctypes.c_size_t),
+        ("pool_peak_bytes", ctypes.c_size_t),
+    ]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -74,6 +105,8 @@ SIGNATURES = {
     "orcha_mesh_get_tile": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "orcha_mesh_load": (_st, [_vp, _vp, _i32, _vp]),
     "orcha_mesh_store": (_st, [_vp, _vp, _i32, _vp]),
+    "orcha_mesh_init_region": (_st, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), _vp]),
     "orcha_packet_create": (_st, [_vp, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp)]),
     "orcha_packet_destroy": (_st, [_vp]),
     "orcha_packet_run": (_st, [_vp, ctypes.c_int, _vp]),
@@ -82,6 +115,11 @@ SIGNATURES = {
     "orcha_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     "orcha_batch_destroy": (_st, [_vp]),
     "orcha_batch_advance": (_st, [_vp, ctypes.c_int, _i32, _i32, _i32, _vp]),
+    "orcha_server_create": (_st, [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]),
+    "orcha_server_destroy": (_st, [_vp]),
+    "orcha_server_submit": (_st, [_vp, ctypes.POINTER(orcha_request_desc), ctypes.POINTER(ctypes.c_int64)]),
+    "orcha_server_wait": (_st, [_vp, ctypes.c_int64, _i32, ctypes.POINTER(orcha_request_stats)]),
+    "orcha_server_get_stats": (_st, [_vp, ctypes.POINTER(orcha_server_stats)]),
     "orcha_autotune": (_st, [_i32, ctypes.POINTER(_i32), ctypes.c_int, _i32, ctypes.c_char_p, ctypes.POINTER(_i32),
                              ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
     "orcha_cfl_dt_noalloc": (_st, [ctypes.POINTER(orcha_mesh_desc), _i32, _vp, _vp]),
@@ -159,6 +197,13 @@ def orcha_mesh_store(mesh: int, interior_ptr: int, host_ptr: bool, stream=None) 
     _check(lib().orcha_mesh_store(mesh, interior_ptr, int(bool(host_ptr)), _stream_ptr(stream)))
 
 
+def orcha_mesh_init_region(mesh: int, kind: int, region, u_in, u_out, stream=None) -> None:
+    r = (_i32 * 4)(*[int(x) for x in region])
+    a = (ctypes.c_double * 5)(*[float(x) for x in u_in])
+    b = (ctypes.c_double * 5)(*[float(x) for x in u_out])
+    _check(lib().orcha_mesh_init_region(mesh, int(kind), r, a, b, _stream_ptr(stream)))
+
+
 def orcha_packet_create(mesh: int, block_ids) -> int:
     ids = np.ascontiguousarray(block_ids, dtype=np.int32)
     h = _vp()
@@ -200,6 +245,34 @@ def orcha_batch_destroy(batch: int) -> None:
 def orcha_batch_advance(batch: int, task: int, nsteps: int, init_dt: bool, use_graph: bool, stream=None) -> None:
     _check(lib().orcha_batch_advance(batch, int(task), int(nsteps), int(bool(init_dt)), int(bool(use_graph)),
                                      _stream_ptr(stream)))
+
+
+def orcha_server_create(hbm_budget_bytes: int, max_active: int = 1024) -> int:
+    h = _vp()
+    _check(lib().orcha_server_create(int(hbm_budget_bytes), int(max_active), ctypes.byref(h)))
+    return h.value
+
+
+def orcha_server_destroy(server: int) -> None:
+    _check(lib().orcha_server_destroy(server))
+
+
+def orcha_server_submit(server: int, req: orcha_request_desc) -> int:
+    t = ctypes.c_int64()
+    _check(lib().orcha_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def orcha_server_wait(server: int, ticket: int, timeout_ms: int = -1) -> orcha_request_stats:
+    st = orcha_request_stats()
+    _check(lib().orcha_server_wait(server, int(ticket), int(timeout_ms), ctypes.byref(st)))
+    return st
+
+
+def orcha_server_get_stats(server: int) -> orcha_server_stats:
+    st = orcha_server_stats()
+    _check(lib().orcha_server_get_stats(server, ctypes.byref(st)))
+    return st
 
 
 DEFAULT_TUNE_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "orcha_b300", "tiles.json")

@@ -224,6 +224,25 @@ orcha_status orcha_mesh_store(orcha_mesh* m, double* interior, int32_t host_ptr,
     return ORCHA_OK;
 }
 
+orcha_status orcha_mesh_init_region(orcha_mesh* m, int32_t kind, const int32_t region[4], const double u_in[5],
+                                    const double u_out[5], void* stream) {
+    if (!m || !region || !u_in || !u_out) return fail(ORCHA_ERR_INVALID, "mesh_init_region: null argument");
+    if (kind != ORCHA_INIT_SPHERE && kind != ORCHA_INIT_HALF_SPACE)
+        return fail(ORCHA_ERR_INVALID, "mesh_init_region: kind must be SPHERE or HALF_SPACE");
+    if (kind == ORCHA_INIT_HALF_SPACE && (region[0] < 0 || region[0] >= m->dev.ndim))
+        return fail(ORCHA_ERR_INVALID, "mesh_init_region: axis outside [0, ndim)");
+    orcha::RegionStates rs;
+    for (int v = 0; v < 5; ++v) {
+        rs.in[v] = u_in[v];
+        rs.out[v] = u_out[v];
+    }
+    ORCHA_CUDA(orcha::launch_region_init(m->dev, m->desc.state_dev[m->cur], kind,
+                                         make_int4(region[0], region[1], region[2], region[3]), rs,
+                                         (cudaStream_t)stream),
+               "mesh_init_region");
+    return ORCHA_OK;
+}
+
 orcha_status orcha_packet_create(orcha_mesh* m, const int32_t* ids, int32_t n, orcha_packet** out) {
     if (!m || !ids || !out) return fail(ORCHA_ERR_INVALID, "packet_create: null argument");
     *out = nullptr;

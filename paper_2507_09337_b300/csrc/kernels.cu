@@ -83,6 +83,14 @@ __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk
     cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
 }
 
+// Every block of the mesh, one CTA per block (no block-id list).
+__global__ void signal_speed_all_kernel(const MeshDev m, const double* __restrict__ U) {
+    __shared__ unsigned long long red[32];
+    const int blk = blockIdx.x;
+    const unsigned long long b = block_signal_speed(m, blk, U);
+    cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
+}
+
 // ---------------------------------------------------------------- dt reduction
 // dt = cfl / max over blocks; then clear the per-block maxima for the next step.
 __global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__ dt) {
@@ -136,6 +144,96 @@ __global__ void synthetic_state_kernel(const MeshDev m, double* __restrict__ U) 
 
 cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st) {
     synthetic_state_kernel<<<148 * 8, 256, 0, st>>>(m, U);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- two-region initial state (serving recipes)
+// Cell (gi, gj, gk) is "inside" when, in half-cell units (centre of cell g at
+// 2g + 1), sum_d (2 g_d + 1 - c2_d)^2 <= r2 (kind 1, sphere), or when g_axis <
+// split (kind 2, half-space). Inside cells take u_in, others u_out: the
+// region test is integer arithmetic and the states are given, so the values
+// are exact and match any other implementation of the same rule.
+__global__ void region_init_kernel(const MeshDev m, double* __restrict__ U, int kind, int4 reg, RegionStates rs) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long blk = e / ncell, c = e % ncell;
+        const int l[3] = {(int)(c % m.bs[0]), (int)((c / m.bs[0]) % m.bs[1]), (int)(c / ((long long)m.bs[0] * m.bs[1]))};
+        const int b[3] = {(int)(blk % m.nb[0]), (int)((blk / m.nb[0]) % m.nb[1]), (int)(blk / ((long long)m.nb[0] * m.nb[1]))};
+        long long g[3];
+        for (int d = 0; d < 3; ++d) g[d] = (long long)b[d] * m.bs[d] + l[d];
+        bool in;
+        if (kind == 1) {
+            const long long c2[3] = {reg.x, reg.y, reg.z};
+            long long d2 = 0;
+            for (int d = 0; d < m.ndim; ++d) {
+                const long long t = 2 * g[d] + 1 - c2[d];
+                d2 += t * t;
+            }
+            in = d2 <= (long long)reg.w;
+        } else {
+            in = g[reg.x] < reg.y;
+        }
+        const int kk = (m.ndim == 3) ? l[2] + kGuard : 0;
+        const long long po = blk * m.blk_stride + ((long long)kk * m.pad[1] + (l[1] + kGuard)) * m.pad[0] + (l[0] + kGuard);
+        for (int v = 0; v < m.nvar; ++v) U[po + v * m.var_stride] = in ? rs.in[v] : rs.out[v];
+    }
+}
+
+// Totals of each conserved variable over the interior cells in a fixed
+// order, so the result depends only on the state: pass 1 sums each block
+// (one CTA per block: per-thread strided sums, then a fixed tree) into
+// partial[blk][v]; pass 2 (one CTA) sums the partials in block order.
+__global__ void block_totals_kernel(const MeshDev m, const double* __restrict__ U, double* __restrict__ partial) {
+    __shared__ double red[256];
+    const int blk = blockIdx.x;
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    for (int v = 0; v < m.nvar; ++v) {
+        double acc = 0.0;
+        for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+            const int kk = (m.ndim == 3) ? k + kGuard : 0;
+            acc += U[(long long)blk * m.blk_stride + v * m.var_stride + ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard)];
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(long long)blk * 5 + v] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void sum_partials_kernel(const MeshDev m, int nblk, const double* __restrict__ partial,
+                                    double* __restrict__ out) {
+    __shared__ double red[256];
+    for (int v = 0; v < m.nvar; ++v) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(long long)b * 5 + v];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[v] = red[0];
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_region_init(const MeshDev& m, double* U, int kind, int4 reg, const RegionStates& rs, cudaStream_t st) {
+    region_init_kernel<<<148 * 4, 256, 0, st>>>(m, U, kind, reg, rs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const MeshDev& m, int nblk, const double* U, double* partial, double* out, cudaStream_t st) {
+    block_totals_kernel<<<(unsigned)nblk, 256, 0, st>>>(m, U, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<1, 256, 0, st>>>(m, nblk, partial, out);
     return cudaGetLastError();
 }
 
@@ -274,6 +372,11 @@ cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, c
 
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st) {
     signal_speed_kernel<<<(unsigned)n, 256, 0, st>>>(m, ids, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st) {
+    signal_speed_all_kernel<<<(unsigned)nblk, 256, 0, st>>>(m, U);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,16 @@ cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cud
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st);
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
+// Signal speed of every block 0..nblk-1 (one CTA per block, no id list).
+cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st);
+// Two conserved states of a two-region initial state (serving recipes).
+struct RegionStates {
+    double in[5], out[5];
+};
+cudaError_t launch_region_init(const MeshDev& m, double* U, int kind, int4 reg, const RegionStates& rs, cudaStream_t st);
+// out[v] = sum over interior cells of conserved variable v (fixed order);
+// partial is scratch of nblk x 5 doubles.
+cudaError_t launch_totals(const MeshDev& m, int nblk, const double* U, double* partial, double* out, cudaStream_t st);
 // Fill the interiors of a padded state with a smooth physical state (autotuning input).
 cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st);
 // Built column-tile variants, widest first.

@@ -21,14 +21,6 @@ namespace orcha {
 // (512 KiB) until the process exits.
 static __device__ __align__(256) unsigned long long g_noalloc_smax[ORCHA_NOALLOC_MAX_BLOCKS];
 
-// One CTA per block of the mesh (no block-id list, which would need memory).
-__global__ void noalloc_signal_speed_kernel(const MeshDev m, const double* __restrict__ U) {
-    __shared__ unsigned long long red[32];
-    const int blk = blockIdx.x;
-    const unsigned long long b = block_signal_speed(m, blk, U);
-    cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
-}
-
 // Device address of g_noalloc_smax on each device, looked up once per device
 // with that device current (host code must never pass the symbol itself).
 static std::mutex g_addr_mu;
@@ -78,8 +70,8 @@ extern "C" orcha_status orcha_cfl_dt_noalloc(const orcha_mesh_desc* desc, int32_
     // the array keeps the previous call's contents: clear the slots this call raises
     cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * (size_t)nblk, s);
     if (e != cudaSuccess) return orcha::cuda_error(e, "cfl_dt_noalloc: clear");
-    orcha::noalloc_signal_speed_kernel<<<(unsigned)nblk, 256, 0, s>>>(m, U);
-    e = cudaGetLastError();
+    // one CTA per block of the mesh (no block-id list, which would need memory)
+    e = orcha::launch_signal_speed_all(m, (int)nblk, U, s);
     if (e != cudaSuccess) return orcha::cuda_error(e, "cfl_dt_noalloc: signal-speed launch");
     e = orcha::launch_dt_reduce(m, (int)nblk, desc->dt_dev, s);
     if (e != cudaSuccess) return orcha::cuda_error(e, "cfl_dt_noalloc: reduce launch");

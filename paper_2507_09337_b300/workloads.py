@@ -286,3 +286,101 @@ def sedov256_uneven_packets(seed: int = 0):
         packets.append(ids[o:o + s])
         o += s
     return spec, packets
+
+
+# ------------------------------------------------------------------ serving requests
+
+def most_cubic(K: int) -> tuple:
+    """Factor K = nbx * nby * nbz with nbx >= nby >= nbz, as close to a cube as
+    possible (smallest nbx - nbz, then smallest nbx)."""
+    best = None
+    for nz in range(1, K + 1):
+        if nz * nz * nz > K:
+            break
+        if K % nz:
+            continue
+        r = K // nz
+        for ny in range(nz, r + 1):
+            if ny * ny > r:
+                break
+            if r % ny:
+                continue
+            nx = r // ny
+            key = (nx - nz, nx)
+            if best is None or key < best[0]:
+                best = (key, (nx, ny, nz))
+    return best[1]
+
+
+def region_mask(spec: MeshSpec, kind: int, region) -> np.ndarray:
+    """Inside-cell mask [k, j, i] of a two-region initial state, with the
+    integer rule of the device recipe: cell g (global index) is inside when
+    sum_d (2 g_d + 1 - region[d])^2 <= region[3] (kind 1, sphere, half-cell
+    units), or when g[region[0]] < region[1] (kind 2, half-space)."""
+    n = spec.ncells
+    gk, gj, gi = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    g = (gi, gj, gk)
+    if kind == 1:
+        d2 = np.zeros(gi.shape, dtype=np.int64)
+        for d in range(spec.ndim):
+            t = 2 * g[d].astype(np.int64) + 1 - int(region[d])
+            d2 += t * t
+        return d2 <= int(region[3])
+    return g[int(region[0])] < int(region[1])
+
+
+def region_state(spec: MeshSpec, kind: int, region, u_in, u_out) -> np.ndarray:
+    """Block array of a two-region initial state (same values as the device recipe)."""
+    mask = region_mask(spec, kind, region)
+    Ug = np.empty((spec.nvar,) + mask.shape)
+    for v in range(spec.nvar):
+        Ug[v] = np.where(mask, u_in[v], u_out[v])
+    return to_blocks(spec, Ug)
+
+
+def _cons(gamma, rho, p, ndim):
+    u = [rho] + [0.0] * ndim + [p / (gamma - 1.0)]
+    return (u + [0.0] * 5)[:5]
+
+
+def serving_request(rng: np.random.Generator, max_blocks: int = 512, sizes=(8, 16, 32), nsteps: int = 1) -> dict:
+    """One serving request: an independent 3D problem of K ~ U[1, max_blocks]
+    blocks of b^3 cells (b ~ U{sizes}) laid out as the most cubic nbx >= nby >=
+    nbz, cubic cells, outflow; Sedov-like (random centre and energy) or
+    Sod-like (random axis and states) initial state as a two-region recipe."""
+    K = int(rng.integers(1, max_blocks + 1))
+    b = int(rng.choice(sizes))
+    nb = most_cubic(K)
+    ncell = [nb[d] * b for d in range(3)]
+    L = max(ncell)
+    spec = MeshSpec(ndim=3, nb=nb, bs=(b, b, b), hi=tuple(c / L for c in ncell))
+    g = spec.gamma
+    if rng.integers(0, 2) == 0:       # Sedov-like
+        kind = 1
+        c2 = [int(rng.integers(2, 2 * n - 1)) for n in ncell]
+        r2 = 49                         # radius 3.5 cells
+        region = (c2[0], c2[1], c2[2], r2)
+        ndep = int(region_mask(spec, kind, region).sum())
+        energy = float(rng.uniform(0.5, 2.0))
+        dV = spec.dx(0) ** 3
+        p0 = 1e-5
+        u_out = _cons(g, 1.0, p0, 3)
+        u_in = list(u_out)
+        u_in[4] = u_out[4] + energy / (ndep * dV)
+    else:                               # Sod-like
+        kind = 2
+        axis = int(rng.integers(0, 3))
+        region = (axis, ncell[axis] // 2, 0, 0)
+        u_in = _cons(g, float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.5, 2.0)), 3)
+        u_out = _cons(g, float(rng.uniform(0.05, 0.5)), float(rng.uniform(0.05, 0.5)), 3)
+    return dict(spec=spec, kind=kind, region=tuple(int(x) for x in region), u_in=tuple(u_in),
+                u_out=tuple(u_out), nsteps=nsteps)
+
+
+def serving_stream(n: int, rate: float, seed_arrivals: int = 1, seed_requests: int = 2, **kw):
+    """n requests with exponential inter-arrival times of mean 1/rate (seconds)
+    and request parameters from serving_request."""
+    ra = np.random.default_rng(seed_arrivals)
+    rr = np.random.default_rng(seed_requests)
+    t = np.cumsum(ra.exponential(1.0 / rate, size=n))
+    return [(float(t[i]), serving_request(rr, **kw)) for i in range(n)]

@@ -1,0 +1,180 @@
+"""Continuous-batching server (orcha_server_*): each request's result is the
+same alone and in the mix (bitwise), the device recipes give the numpy initial
+states, admission waits for memory under a tight budget, and a served request
+matches the oracle and the plain packet path."""
+import numpy as np
+import pytest
+
+from paper_2507_09337_b300 import binding as B
+from paper_2507_09337_b300 import serve
+from paper_2507_09337_b300 import workloads as wl
+
+from .gpu_helpers import oracle_steps, rule12_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_09337_b300 import build
+    build.build()
+
+
+def _requests(n, seed, max_blocks=8, sizes=(8, 16), nsteps=3):
+    rng = np.random.default_rng(seed)
+    return [wl.serving_request(rng, max_blocks=max_blocks, sizes=sizes, nsteps=nsteps) for _ in range(n)]
+
+
+def _host_buffers(req):
+    import torch
+    spec = req["spec"]
+    U0 = wl.region_state(spec, req["kind"], req["region"], req["u_in"], req["u_out"])
+    init = torch.from_numpy(U0).pin_memory()
+    out = torch.empty(spec.block_shape(), dtype=torch.float64).pin_memory()
+    return U0, init, out
+
+
+def _serve(reqs, task=B.ORCHA_TASK_HYDRO_FP64, budget=8 << 30, together=True, from_host=True):
+    """Run requests through one server; returns (outputs, stats)."""
+    srv = serve.Server(budget)
+    keep, outs, stats = [], [], []
+    try:
+        descs = []
+        for r in reqs:
+            if from_host:
+                U0, init, out = _host_buffers(r)
+                keep.append((init, out))
+                descs.append(serve.request_desc(r, task, init.data_ptr(), out.data_ptr()))
+                outs.append(out)
+            else:
+                import torch
+                out = torch.empty(r["spec"].block_shape(), dtype=torch.float64).pin_memory()
+                keep.append(out)
+                descs.append(serve.request_desc(r, task, None, out.data_ptr()))
+                outs.append(out)
+        if together:
+            tickets = [srv.submit(d) for d in descs]
+            stats = [srv.wait(t) for t in tickets]
+        else:
+            stats = [srv.wait(srv.submit(d)) for d in descs]
+        peak = srv.stats().pool_peak_bytes
+    finally:
+        srv.close()
+    return [o.numpy().copy() for o in outs], stats, peak
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    reqs = _requests(8, 3)
+    alone = [_serve([r])[0][0] for r in reqs]
+    mixed, stats, _ = _serve(reqs)
+    for a, m, s in zip(alone, mixed, stats):
+        assert s.status == 0 and s.device_error == 0
+        assert np.array_equal(a, m)
+
+
+def test_mixed_precision_and_block_sizes_in_flight_together():
+    reqs = _requests(6, 5, sizes=(8, 16, 32), max_blocks=4, nsteps=2)
+    a64 = [_serve([r])[0][0] for r in reqs[:3]]
+    a32 = [_serve([r], task=B.ORCHA_TASK_HYDRO_F32FLUX)[0][0] for r in reqs[3:]]
+    srv = serve.Server(8 << 30)
+    try:
+        keep, tickets = [], []
+        for i, r in enumerate(reqs):
+            U0, init, out = _host_buffers(r)
+            keep.append((init, out))
+            task = B.ORCHA_TASK_HYDRO_FP64 if i < 3 else B.ORCHA_TASK_HYDRO_F32FLUX
+            tickets.append(srv.submit(serve.request_desc(r, task, init.data_ptr(), out.data_ptr())))
+        for t in tickets:
+            srv.wait(t)
+    finally:
+        srv.close()
+    for (init, out), a in zip(keep, a64 + a32):
+        assert np.array_equal(out.numpy(), a)
+
+
+def test_device_recipe_equals_host_initial_state():
+    reqs = _requests(4, 7)
+    host, _, _ = _serve(reqs, from_host=True)
+    recipe, stats, _ = _serve(reqs, from_host=False)
+    for h, r, s in zip(host, recipe, stats):
+        assert np.array_equal(h, r)
+        nv = 5
+        tot = r.sum(axis=(0, 2, 3, 4))
+        np.testing.assert_allclose(s.totals[:nv], tot, rtol=1e-12, atol=1e-12 * np.abs(tot).max())
+
+
+def test_admission_waits_for_memory_under_a_tight_budget():
+    reqs = _requests(6, 11, max_blocks=8, sizes=(16,))
+    need = max(2 * r["spec"].nblocks * 5 * 20 ** 3 * 8 for r in reqs)
+    budget = int(2.2 * need) + (1 << 20)
+    alone = [_serve([r])[0][0] for r in reqs]
+    mixed, stats, peak = _serve(reqs, budget=budget)
+    assert peak <= budget
+    assert all(s.t_admit_us >= 0 for s in stats)
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a, m)
+
+
+def test_served_request_matches_oracle_and_packet_path(oracle_mod):
+    req = _requests(1, 13, max_blocks=6, sizes=(8,), nsteps=4)[0]
+    spec = req["spec"]
+    U0 = wl.region_state(spec, req["kind"], req["region"], req["u_in"], req["u_out"])
+    (G,), (s,), _ = _serve([req])
+    O, dts = oracle_steps(oracle_mod, spec, U0, 4)
+    assert rule12_error(G, O, spec.nvar) <= 1e-12
+    m = oracle_mod.Mesh(**spec.oracle_kwargs())
+    assert s.dt_next == pytest.approx(oracle_mod.dt(m, O), rel=1e-12)
+    from .gpu_helpers import gpu_steps
+    P, _, _ = gpu_steps(spec, U0, 4)
+    assert np.array_equal(G, P)
+
+
+def test_submit_validation_and_timeout():
+    import torch
+    srv = serve.Server(64 << 20)
+    try:
+        big = wl.serving_request(np.random.default_rng(1), max_blocks=1, sizes=(32,))
+        big["spec"] = wl.MeshSpec(ndim=3, nb=(4, 4, 4), bs=(32, 32, 32))
+        with pytest.raises(B.OrchaError) as ei:
+            srv.submit(serve.request_desc(big, B.ORCHA_TASK_HYDRO_FP64))
+        assert ei.value.status == B.ORCHA_ERR_OOM
+        bad = dict(big, nsteps=0)
+        bad["spec"] = wl.MeshSpec(ndim=3, nb=(1, 1, 1), bs=(8, 8, 8))
+        with pytest.raises(B.OrchaError) as ei:
+            srv.submit(serve.request_desc(bad, B.ORCHA_TASK_HYDRO_FP64))
+        assert ei.value.status == B.ORCHA_ERR_INVALID
+        slow = dict(bad, nsteps=400)
+        slow["spec"] = wl.MeshSpec(ndim=3, nb=(2, 1, 1), bs=(32, 32, 32))
+        t = srv.submit(serve.request_desc(slow, B.ORCHA_TASK_HYDRO_FP64))
+        with pytest.raises(B.OrchaError) as ei:
+            srv.wait(t, 0)
+        assert ei.value.status == B.ORCHA_ERR_TIMEOUT
+        st = srv.wait(t)                       # the ticket survives the timeout
+        assert st.zone_updates == 2 * 32 ** 3 * 400
+    finally:
+        srv.close()
+
+
+def test_nonphysical_request_reports_device_error():
+    import torch
+    spec = wl.MeshSpec(ndim=3, nb=(2, 1, 1), bs=(8, 8, 8))
+    U0 = wl.uniform_state(spec, 1.0, (0.0, 0.0, 0.0), 1.0)
+    U0[0, 4, 2, 2, 2] = -1.0
+    init = torch.from_numpy(U0).pin_memory()
+    out = torch.empty_like(init).pin_memory()
+    req = dict(spec=spec, kind=0, region=(0, 0, 0, 0), u_in=(0,) * 5, u_out=(0,) * 5, nsteps=1)
+    srv = serve.Server(64 << 20)
+    try:
+        t = srv.submit(serve.request_desc(req, B.ORCHA_TASK_HYDRO_FP64, init.data_ptr(), out.data_ptr()))
+        with pytest.raises(B.OrchaError) as ei:
+            srv.wait(t)
+        assert ei.value.status == B.ORCHA_ERR_NONFINITE
+        # the server keeps serving after a failed request
+        good = _requests(1, 17)[0]
+        t2 = srv.submit(serve.request_desc(good, B.ORCHA_TASK_HYDRO_FP64))
+        assert srv.wait(t2).status == 0
+    finally:
+        srv.close()
