@@ -327,6 +327,17 @@ ORCHA_API orcha_status orcha_cfl_dt_noalloc(const orcha_mesh_desc* desc, int32_t
  * none) and clear it. Returns NONFINITE / TIMEOUT when a bit is set. */
 ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* device_error);
 
+/* Diagnostics: the FP32-flux task converts between binary64 and binary32 on
+ * the integer pipe (bit-field arithmetic from the IEEE-754 formats, with the
+ * hardware conversion for subnormal, infinite and NaN cases). This checks
+ * them against the hardware conversions on the current device: binary32 ->
+ * binary64 for the `count` patterns starting at first_pattern, and binary64 ->
+ * binary32 (round to nearest even) for `count` pseudo-random patterns derived
+ * from `seed`; *mismatches receives the number of results whose bits differ
+ * (NaN payloads excepted). Synchronous. Errors: INVALID, CUDA. */
+ORCHA_API orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64_t count, uint64_t seed,
+                                                  uint64_t* mismatches);
+
 /* Message of the last error returned on this thread ("" if none). */
 ORCHA_API const char* orcha_last_error(void);
 

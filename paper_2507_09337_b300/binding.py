@@ -124,6 +124,8 @@ SIGNATURES = {
                              ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
     "orcha_cfl_dt_noalloc": (_st, [ctypes.POINTER(orcha_mesh_desc), _i32, _vp, _vp]),
     "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
+    "orcha_selftest_conversions": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
 
@@ -301,6 +303,12 @@ def orcha_mesh_poll(mesh: int, stream=None) -> int:
     err = _i32()
     _check(lib().orcha_mesh_poll(mesh, _stream_ptr(stream), ctypes.byref(err)))
     return err.value
+
+
+def orcha_selftest_conversions(first_pattern: int, count: int, seed: int = 1) -> int:
+    bad = ctypes.c_uint64()
+    _check(lib().orcha_selftest_conversions(int(first_pattern), int(count), int(seed), ctypes.byref(bad)))
+    return bad.value
 
 
 def orcha_last_error() -> str:

@@ -87,12 +87,48 @@ template <> struct P<rd> {
     static __device__ __forceinline__ double to_double(rd x) { return x.v; }
 };
 
+// ---------------------------------------------------------------- IEEE-754 format conversions on the integer pipe
+// Written from the binary64/binary32 layouts (sign | biased exponent |
+// fraction). Bitwise equal to the hardware conversions for every input: the
+// integer paths cover zeros and normal results, the rest (subnormal, inf,
+// NaN) falls back to the hardware conversion, which on this GPU issues on
+// the FP64 pipe.
+
+// binary64 -> binary32, round to nearest even.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if (a == 0) return __uint_as_float(sign);
+    const int e = (int)(a >> 52);                        // biased binary64 exponent
+    if (e >= 897 && e <= 1150) {                         // binary32 normal range: 2^-126 .. 2^127
+        const unsigned long long m = a & 0xFFFFFFFFFFFFFull;
+        unsigned r = ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
+        const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);          // the 29 dropped fraction bits
+        r += (rem > 0x10000000u) || (rem == 0x10000000u && (r & 1u));  // a carry may reach the exponent
+        return __uint_as_float(sign | r);
+    }
+    return __double2float_rn(x);
+}
+
+// binary32 -> binary64 (exact).
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned a = b & 0x7FFFFFFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (a == 0) return __longlong_as_double((long long)sign);
+    if (a >= 0x00800000u && a < 0x7F800000u)             // normal: rebias 127 -> 1023
+        return __longlong_as_double((long long)(sign | (((unsigned long long)a + (896ull << 23)) << 29)));
+    return (double)x;
+}
+
 template <> struct P<float> {
     using store = float;
-    static __device__ __forceinline__ float in(double x) { return __double2float_rn(x); }
+    static __device__ __forceinline__ float in(double x) { return d2f_rn(x); }
     static __device__ __forceinline__ float out(float x) { return x; }
-    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-    static __device__ __forceinline__ float sqrt(float x) { return __fsqrt_rn(x); }
+    // hardware approximations (about 1 ulp): the FP32 flux path states its error against FP64
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float x) { *p = x; }
     static __device__ __forceinline__ bool pos(float x) { return x > 0.0f; }
@@ -107,8 +143,36 @@ template <> struct P<float> {
     }
     static __device__ __forceinline__ float half(float x) { return 0.5f * x; }
     static __device__ __forceinline__ float zero() { return 0.0f; }
-    static __device__ __forceinline__ double to_double(float x) { return (double)x; }
+    static __device__ __forceinline__ double to_double(float x) { return f2d(x); }
 };
+
+// ---------------------------------------------------------------- float-float (error-free transformations)
+// A value carried as an unevaluated sum hi + lo of two floats (about 46
+// significant bits). two_sum (Knuth) and two_prod (with FMA) are exact.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+// c * (hi + lo) for a float-float constant c = ch + cl, as an unnormalised pair.
+__device__ __forceinline__ ff ff_scale(ff d, float ch, float cl) {
+    const float p = d.hi * ch;
+    const float pe = fmaf(d.hi, ch, -p);                  // d.hi * ch = p + pe exactly
+    return {p, fmaf(d.hi, cl, fmaf(d.lo, ch, pe))};
+}
+// (a.hi + a.lo) + (b.hi + b.lo), renormalised.
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    const float lo = s.lo + (a.lo + b.lo);
+    const float hi = s.hi + lo;
+    return {hi, lo - (hi - s.hi)};
+}
+// Exact difference a - b of two floats as a float-float.
+__device__ __forceinline__ ff ff_diff(float a, float b) { return two_sum(a, -b); }
+__device__ __forceinline__ double ff_to_double(ff a) { return __dadd_rn(f2d(a.hi), f2d(a.lo)); }
 
 // ---------------------------------------------------------------- mesh as the kernels see it
 struct MeshDev {

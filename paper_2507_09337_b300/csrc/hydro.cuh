@@ -27,6 +27,8 @@
 // ring of predicted states and their boundary faces.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace orcha {
@@ -131,6 +133,40 @@ __device__ __forceinline__ unsigned long long block_signal_speed(const MeshDev& 
         smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
     }
     return smaxb;
+}
+
+// Signal speed sum_d (|u_d| + c) / dx_d of one new FP64 state, as the bits of
+// a non-negative double; raises the non-physical flag. FP64 path: the
+// definition's expression tree. FP32-flux path: evaluated in FP32 from the
+// state rounded to nearest and rounded up by a factor 1 + 2^-18 (above the
+// few-ulp error of that evaluation), so dt = cfl / max never exceeds the FP64
+// value by more than rounding; a cell whose FP32 pressure is not positive is
+// re-evaluated in FP64 (cancellation in E - |m|^2/(2 rho)).
+template <class T, int NDIM>
+__device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, const rd* Un) {
+    constexpr int NV = NDIM + 2;
+    if constexpr (std::is_same<T, float>::value) {
+        float U[NV], W[NV], r;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = d2f_rn(Un[v].v);
+        prim_from_cons<float, NDIM>(U, W, r, d2f_rn(m.gm1));
+        if (W[0] > 0.0f && W[NV - 1] > 0.0f) {
+            const float c = P<float>::sqrt((d2f_rn(m.gamma) * W[NV - 1]) * r);
+            float s = (fabsf(W[1]) + c) * d2f_rn(m.idx[0]);
+#pragma unroll
+            for (int d = 1; d < NDIM; ++d) s = s + (fabsf(W[1 + d]) + c) * d2f_rn(m.idx[d]);
+            s = s * 1.0000038146972656f;                     // 1 + 2^-18
+            return (unsigned long long)__double_as_longlong(f2d(s));
+        }
+    }
+    rd W[NV], r;
+    prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
+    if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[NV - 1]))) atomicOr(m.err, 1);
+    const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
+    rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
+#pragma unroll
+    for (int d = 1; d < NDIM; ++d) s = s + ((rd(fabs(W[1 + d].v)) + c) * rd(m.idx[d]));
+    return (unsigned long long)bits(s);   // s >= 0 or NaN
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -313,12 +349,31 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     };
 
     // z state carried by the owner: high-z face state of the previous plane,
-    // its low-z face flux, and its x+y flux sum
+    // its low-z face flux, and its x+y flux-difference sum. FP64 path: the sum
+    // in FP64 from the promoted face fluxes, as the definition writes it.
+    // FP32-flux path: each difference c_d (F_hi - F_lo) of FP32 face fluxes is
+    // formed exactly (two_sum) and scaled by c_d held as a float pair, and the
+    // x, y, z terms are summed as float-float (about 46 bits); only the final
+    // U+ = U - (sum) is FP64 arithmetic. The same face value enters both cells,
+    // so the sum still telescopes to ~1e-14 of each term.
+    constexpr bool F32 = std::is_same<T, float>::value;
     T zp_prev[NV], Fz_prev[NV];
     double acc_prev[NV];
+    ff acc_ff[NV];
     unsigned long long smaxb = 0ull;   // bits of the largest signal speed
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { zp_prev[v] = P<T>::zero(); Fz_prev[v] = P<T>::zero(); acc_prev[v] = 0.0; }
+    for (int v = 0; v < NV; ++v) {
+        zp_prev[v] = P<T>::zero();
+        Fz_prev[v] = P<T>::zero();
+        acc_prev[v] = 0.0;
+        acc_ff[v] = {0.0f, 0.0f};
+    }
+    float ch[3], cl[3];                  // c_d = dt/dx_d as float pairs (FP32-flux path)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ch[d] = d2f_rn(cd[d]);
+        cl[d] = F32 ? d2f_rn(__dsub_rn(cd[d], f2d(ch[d]))) : 0.0f;
+    }
 
     const int pbeg = (NDIM == 3) ? -1 : 0, pend = (NDIM == 3) ? bz : 0;
     if (NDIM == 3) { load_plane(-2); load_plane(-1); }
@@ -413,50 +468,48 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 rd Un[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
-                    const rd acc = rd(acc_prev[v]) + tz;
-                    Un[v] = rd(Ub[gi + v * vs]) - acc;
+                    if constexpr (F32) {
+                        const ff tz = ff_scale(ff_diff(Fz[v], Fz_prev[v]), ch[2], cl[2]);
+                        Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
+                    } else {
+                        const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
+                        const rd acc = rd(acc_prev[v]) + tz;
+                        Un[v] = rd(Ub[gi + v * vs]) - acc;
+                    }
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                // signal speed of the new state
-                rd W[NV], r;
-                prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
-                if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[NV - 1]))) atomicOr(m.err, 1);
-                const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
-                rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
-#pragma unroll
-                for (int d = 1; d < NDIM; ++d) s = s + ((rd(fabs(W[1 + d].v)) + c) * rd(m.idx[d]));
-                smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
+                smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
         }
         if (inner) {
-            // x then y flux differences of plane p (FP64)
+            // x then y flux differences of plane p
             const int fx = tj * (TX + 1) + ti, fy = tj * TX + ti;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx + 1]))) -
-                                           rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx]))));
-                const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy + TX]))) -
-                                           rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy]))));
-                acc_prev[v] = (tx + ty).v;
+                if constexpr (F32) {
+                    const ff tx = ff_scale(ff_diff(sFx[v * Tl::NXF + fx + 1], sFx[v * Tl::NXF + fx]), ch[0], cl[0]);
+                    const ff ty = ff_scale(ff_diff(sFy[v * Tl::NYF + fy + TX], sFy[v * Tl::NYF + fy]), ch[1], cl[1]);
+                    acc_ff[v] = ff_add(tx, ty);
+                } else {
+                    const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx + 1]))) -
+                                               rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx]))));
+                    const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy + TX]))) -
+                                               rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy]))));
+                    acc_prev[v] = (tx + ty).v;
+                }
             }
             if (NDIM == 2) {
                 const long long gi = ((long long)(y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
                 rd Un[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
+                    if constexpr (F32) Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(acc_ff[v]));
+                    else Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                rd W[NV], r;
-                prim_from_cons<rd, NDIM>(Un, W, r, rd(m.gm1));
-                if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[NV - 1]))) atomicOr(m.err, 1);
-                const rd c = P<rd>::sqrt((rd(m.gamma) * W[NV - 1]) * r);
-                rd s = (rd(fabs(W[1].v)) + c) * rd(m.idx[0]);
-                s = s + ((rd(fabs(W[2].v)) + c) * rd(m.idx[1]));
-                smaxb = umax64(smaxb, (unsigned long long)bits(s));   // s >= 0 or NaN
+                smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
             }
         }
     }

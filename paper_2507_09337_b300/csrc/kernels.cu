@@ -237,6 +237,44 @@ cudaError_t launch_totals(const MeshDev& m, int nblk, const double* U, double* p
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- self-test of the integer-pipe conversions
+// f2d on every binary32 pattern in [lo, lo + n) and d2f_rn on patterns from a
+// 64-bit mixing function (splitmix64) plus exponents near the binary32 range
+// edges; counts results whose bits differ from the hardware conversion.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void selftest_kernel(unsigned long long lo, unsigned long long n, unsigned long long seed,
+                                unsigned long long* bad) {
+    unsigned long long cnt = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned fb = (unsigned)(lo + i);
+        const float f = __uint_as_float(fb);
+        const double a = f2d(f), b = (double)f;
+        if (__double_as_longlong(a) != __double_as_longlong(b) && !(a != a && b != b)) ++cnt;
+        unsigned long long db = mix64(seed + i);
+        if (i & 1) {   // steer half of the samples to exponents around the binary32 normal range
+            const unsigned long long e = 880 + (mix64(db) % 290);
+            db = (db & 0x800FFFFFFFFFFFFFull) | (e << 52);
+        }
+        const double d = __longlong_as_double((long long)db);
+        const float x = d2f_rn(d), y = __double2float_rn(d);
+        if (__float_as_uint(x) != __float_as_uint(y) && !(x != x && y != y)) ++cnt;
+    }
+    if (cnt) atomicAdd(bad, cnt);
+}
+
+cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigned long long seed,
+                            unsigned long long* bad, cudaStream_t st) {
+    selftest_kernel<<<148 * 16, 256, 0, st>>>(lo, n, seed, bad);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- hydro launch table
 template <int NDIM, int TX, int TY, class T>
 static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,
