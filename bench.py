@@ -237,8 +237,8 @@ def main():
     tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
     batch = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
     hydro_events = []
-    # per bench step: pack, signal speed of every packet, dt reduce, nt persistent launches, unpack
-    launches_per_step = 1 + npk + 1 + nt + 1
+    # per bench step: pack, signal speed (one launch), dt reduce, nt persistent launches, unpack
+    launches_per_step = 1 + 1 + 1 + nt + 1
 
     def step(record: bool):
         B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)

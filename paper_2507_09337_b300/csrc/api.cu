@@ -312,8 +312,9 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
                                   int init_dt, void* stream) {
     orcha_status s;
     if (init_dt) {
-        for (int i = 0; i < npk; ++i)
-            if ((s = orcha_packet_run(pk[i], ORCHA_TASK_SIGNAL_SPEED, stream))) return s;
+        // the packets cover every block: one launch over the whole mesh
+        ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], (cudaStream_t)stream),
+                   "advance signal speed");
         if ((s = orcha_dt_reduce(m, stream))) return s;
     }
     for (int n = 0; n < nsteps; ++n) {
@@ -516,10 +517,12 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
     cudaStream_t st = (cudaStream_t)stream;
     orcha_status s;
     if (init_dt) {
-        for (auto* p : b->packets)
-            if ((s = orcha_packet_run(const_cast<orcha_packet*>(p), ORCHA_TASK_SIGNAL_SPEED, stream))) return s;
-        for (auto* m : b->meshes)
+        // one launch per mesh over all its blocks (the batch covers every block)
+        for (auto* m : b->meshes) {
+            ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st),
+                       "batch signal speed");
             if ((s = orcha_dt_reduce(m, stream))) return s;
+        }
     }
     // the device copy of each mesh's current buffer index, as of this point in the stream
     std::vector<int> cur(b->meshes.size());

@@ -89,26 +89,40 @@ template <> struct P<rd> {
 
 // ---------------------------------------------------------------- IEEE-754 format conversions on the integer pipe
 // Written from the binary64/binary32 layouts (sign | biased exponent |
-// fraction). Bitwise equal to the hardware conversions for every input: the
-// integer paths cover zeros and normal results, the rest (subnormal, inf,
-// NaN) falls back to the hardware conversion, which on this GPU issues on
-// the FP64 pipe.
+// fraction), entirely in integer arithmetic -- including zeros, subnormals,
+// overflow, infinities and NaN -- so no conversion instruction issues on the
+// FP64 pipe (even a predicated-off one). Bitwise equal to the hardware
+// conversions (NaN payloads aside); checked on the GPU by
+// orcha_selftest_conversions.
 
-// binary64 -> binary32, round to nearest even.
+// binary64 -> binary32, round to nearest, ties to even.
 __device__ __forceinline__ float d2f_rn(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    if (a == 0) return __uint_as_float(sign);
     const int e = (int)(a >> 52);                        // biased binary64 exponent
-    if (e >= 897 && e <= 1150) {                         // binary32 normal range: 2^-126 .. 2^127
-        const unsigned long long m = a & 0xFFFFFFFFFFFFFull;
-        unsigned r = ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
+    const unsigned long long m = a & 0xFFFFFFFFFFFFFull;
+    unsigned r;
+    if (e >= 897 && e <= 1150) {                         // normal binary32 result (or overflow by rounding)
+        r = ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
         const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);          // the 29 dropped fraction bits
         r += (rem > 0x10000000u) || (rem == 0x10000000u && (r & 1u));  // a carry may reach the exponent
-        return __uint_as_float(sign | r);
+    } else if (e > 1150) {                               // overflow to infinity, or inf / NaN
+        r = 0x7F800000u | ((e == 2047 && m) ? (0x00400000u | (unsigned)(m >> 29)) : 0u);
+    } else if (e == 0 && m == 0) {                       // zero
+        r = 0u;
+    } else {                                             // subnormal binary32 result (units of 2^-149)
+        const unsigned long long full = (e ? (1ull << 52) : 0ull) | m;
+        const int shift = (e ? 926 - e : 925);           // value = full * 2^(shift_base) -> units of 2^-149
+        if (shift >= 64) {
+            r = 0u;
+        } else {
+            r = (unsigned)(full >> shift);
+            const unsigned long long rem = full & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+            r += (rem > half) || (rem == half && (r & 1u));
+        }
     }
-    return __double2float_rn(x);
+    return __uint_as_float(sign | r);
 }
 
 // binary32 -> binary64 (exact).
@@ -116,15 +130,48 @@ __device__ __forceinline__ double f2d(float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned a = b & 0x7FFFFFFFu;
     const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    if (a == 0) return __longlong_as_double((long long)sign);
-    if (a >= 0x00800000u && a < 0x7F800000u)             // normal: rebias 127 -> 1023
-        return __longlong_as_double((long long)(sign | (((unsigned long long)a + (896ull << 23)) << 29)));
+    unsigned long long r;
+    if (a >= 0x00800000u && a < 0x7F800000u) {          // normal: rebias 127 -> 1023
+        r = ((unsigned long long)a + (896ull << 23)) << 29;
+    } else if (a >= 0x7F800000u) {                      // inf / NaN
+        r = 0x7FF0000000000000ull | ((unsigned long long)(a & 0x007FFFFFu) << 29) |
+            ((a & 0x007FFFFFu) ? 0x0008000000000000ull : 0ull);
+    } else if (a == 0u) {
+        r = 0ull;
+    } else {                                            // subnormal: a * 2^-149, normalise
+        const int p = 31 - __clz((int)a);               // leading bit, 0..22
+        r = ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)a << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
+    return __longlong_as_double((long long)(sign | r));
+}
+
+// Which conversion the FP32-flux path issues: the integer-pipe forms above
+// (1) or the hardware conversions (0). Both are exact, so results do not
+// depend on the choice; it trades FP64-pipe slots against integer
+// instructions.
+#ifndef ORCHA_CONVERT_ON_INT_PIPE
+#define ORCHA_CONVERT_ON_INT_PIPE 0
+#endif
+
+__device__ __forceinline__ float to_f32(double x) {
+#if ORCHA_CONVERT_ON_INT_PIPE
+    return d2f_rn(x);
+#else
+    return __double2float_rn(x);
+#endif
+}
+
+__device__ __forceinline__ double to_f64(float x) {
+#if ORCHA_CONVERT_ON_INT_PIPE
+    return f2d(x);
+#else
     return (double)x;
+#endif
 }
 
 template <> struct P<float> {
     using store = float;
-    static __device__ __forceinline__ float in(double x) { return d2f_rn(x); }
+    static __device__ __forceinline__ float in(double x) { return to_f32(x); }
     static __device__ __forceinline__ float out(float x) { return x; }
     // hardware approximations (about 1 ulp): the FP32 flux path states its error against FP64
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
@@ -143,7 +190,7 @@ template <> struct P<float> {
     }
     static __device__ __forceinline__ float half(float x) { return 0.5f * x; }
     static __device__ __forceinline__ float zero() { return 0.0f; }
-    static __device__ __forceinline__ double to_double(float x) { return f2d(x); }
+    static __device__ __forceinline__ double to_double(float x) { return to_f64(x); }
 };
 
 // ---------------------------------------------------------------- float-float (error-free transformations)
@@ -172,7 +219,7 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 }
 // Exact difference a - b of two floats as a float-float.
 __device__ __forceinline__ ff ff_diff(float a, float b) { return two_sum(a, -b); }
-__device__ __forceinline__ double ff_to_double(ff a) { return __dadd_rn(f2d(a.hi), f2d(a.lo)); }
+__device__ __forceinline__ double ff_to_double(ff a) { return __dadd_rn(to_f64(a.hi), to_f64(a.lo)); }
 
 // ---------------------------------------------------------------- mesh as the kernels see it
 struct MeshDev {

@@ -148,15 +148,15 @@ __device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, 
     if constexpr (std::is_same<T, float>::value) {
         float U[NV], W[NV], r;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) U[v] = d2f_rn(Un[v].v);
-        prim_from_cons<float, NDIM>(U, W, r, d2f_rn(m.gm1));
+        for (int v = 0; v < NV; ++v) U[v] = to_f32(Un[v].v);
+        prim_from_cons<float, NDIM>(U, W, r, to_f32(m.gm1));
         if (W[0] > 0.0f && W[NV - 1] > 0.0f) {
-            const float c = P<float>::sqrt((d2f_rn(m.gamma) * W[NV - 1]) * r);
-            float s = (fabsf(W[1]) + c) * d2f_rn(m.idx[0]);
+            const float c = P<float>::sqrt((to_f32(m.gamma) * W[NV - 1]) * r);
+            float s = (fabsf(W[1]) + c) * to_f32(m.idx[0]);
 #pragma unroll
-            for (int d = 1; d < NDIM; ++d) s = s + (fabsf(W[1 + d]) + c) * d2f_rn(m.idx[d]);
+            for (int d = 1; d < NDIM; ++d) s = s + (fabsf(W[1 + d]) + c) * to_f32(m.idx[d]);
             s = s * 1.0000038146972656f;                     // 1 + 2^-18
-            return (unsigned long long)__double_as_longlong(f2d(s));
+            return (unsigned long long)__double_as_longlong(to_f64(s));
         }
     }
     rd W[NV], r;
@@ -243,34 +243,64 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     }
 
     // L: primitives of plane pz (interior z index, -2 .. bz+1) into its ring slot
+    // Source of each R2 cell this thread loads. The x/y part of the halo
+    // mapping is the same on every plane, so it is resolved once: the source
+    // block's (x, y) index times the block stride plus the in-block offset of
+    // the source column. Per plane only the z part is added (uniform over the
+    // CTA). GATHER = false reads the padded block itself.
+    constexpr int KMAX = (R2N + NT - 1) / NT;
+    long long base_xy[KMAX];
+    unsigned interior_mask = 0;           // bit k: cell k is an interior column of the tile
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int c = tid + k * NT;
+        const int ci = c % R2X, cj = c / R2X;
+        int sbx = bc[0], sby = bc[1], sx = x0 + ci, sy = y0 + cj;
+        if (GATHER) {
+            const int l[2] = {x0 + ci - kGuard, y0 + cj - kGuard};
+            int sb[2], sl[2];
+#pragma unroll
+            for (int d = 0; d < 2; ++d) {
+                const int n = m.nb[d] * m.bs[d];
+                int gi = bc[d] * m.bs[d] + l[d];
+                if (l[d] < 0 || l[d] >= m.bs[d]) {
+                    if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+                    else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+                }
+                sb[d] = gi / m.bs[d];
+                sl[d] = gi % m.bs[d] + kGuard;
+            }
+            sbx = sb[0]; sby = sb[1]; sx = sl[0]; sy = sl[1];
+        }
+        base_xy[k] = (sbx + (long long)m.nb[0] * sby) * m.blk_stride + ((long long)sy * px + sx);
+        if (ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2) interior_mask |= 1u << k;
+    }
+    const long long nbxy_stride = (long long)m.nb[0] * m.nb[1] * m.blk_stride;
+    const long long plane = (long long)py * px;
+
+    // L: primitives of plane pzi (interior z index, -2 .. bz+1) into its ring slot
     auto load_plane = [&](int pzi) {
         const int slot = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
         S* w = sW + slot * NW * R2N;
-        const int zz = (NDIM == 3) ? pzi + kGuard : 0;
-        for (int c = tid; c < R2N; c += NT) {
-            const int ci = c % R2X, cj = c / R2X;
-            const double* src = Ub + (((long long)zz * py + (y0 + cj)) * px + (x0 + ci));
-            if (GATHER) {
-                const int l[3] = {x0 + ci - kGuard, y0 + cj - kGuard, pzi};
-                bool outside = false;
-#pragma unroll
-                for (int d = 0; d < NDIM; ++d) outside |= (l[d] < 0) | (l[d] >= m.bs[d]);
-                if (outside) {
-                    int sb[3] = {0, 0, 0}, sl[3] = {0, 0, 0};
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) {
-                        const int n = m.nb[d] * m.bs[d];
-                        int gi = bc[d] * m.bs[d] + l[d];
-                        if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
-                        else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
-                        sb[d] = gi / m.bs[d];
-                        sl[d] = gi % m.bs[d] + kGuard;
-                    }
-                    const long long sblk = sb[0] + (long long)m.nb[0] * (sb[1] + (long long)m.nb[1] * sb[2]);
-                    const int sz = (NDIM == 3) ? sl[2] : 0;
-                    src = Uin + sblk * m.blk_stride + (((long long)sz * py + sl[1]) * px + sl[0]);
-                }
+        long long zoff = 0;                     // z part of the source offset (2D: 0)
+        if (NDIM == 3) {
+            int sbz = bc[2], sz = pzi + kGuard;
+            if (GATHER && (pzi < 0 || pzi >= bz)) {
+                const int n = m.nb[2] * m.bs[2];
+                int gi = bc[2] * m.bs[2] + pzi;
+                if (m.periodic[2]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+                else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+                sbz = gi / m.bs[2];
+                sz = gi % m.bs[2] + kGuard;
             }
+            zoff = sbz * nbxy_stride + sz * plane;
+        }
+        const bool zin = pzi >= 0 && pzi < bz;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int c = tid + k * NT;
+            if (c >= R2N) break;
+            const double* src = Uin + base_xy[k] + zoff;
             T U[NV], W[NV], r;
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[v] = P<T>::in(src[v * vs]);
@@ -278,8 +308,8 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 #pragma unroll
             for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
             P<T>::st(&w[NV * R2N + c], r);
-            const bool interior = ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2 && pzi >= 0 && pzi < bz;
-            if (interior && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1]))) atomicOr(m.err, 1);
+            if (zin && ((interior_mask >> k) & 1u) && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1])))
+                atomicOr(m.err, 1);
         }
     };
 
@@ -372,7 +402,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         ch[d] = d2f_rn(cd[d]);
-        cl[d] = F32 ? d2f_rn(__dsub_rn(cd[d], f2d(ch[d]))) : 0.0f;
+        cl[d] = F32 ? d2f_rn(__dsub_rn(cd[d], to_f64(ch[d]))) : 0.0f;
     }
 
     const int pbeg = (NDIM == 3) ? -1 : 0, pend = (NDIM == 3) ? bz : 0;
@@ -406,10 +436,12 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         if (inner && tid < Tl::NRING) {
             T flo[3][NV], fhi[3][NV];
             predict(p, rc2, flo, fhi);
-            const int d = rface >> 1;
+            // the one face state this ring cell contributes (selects keep the arrays in registers)
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], (rface & 1) ? fhi[d][v] : flo[d][v]);
+            for (int v = 0; v < NV; ++v) {
+                const T val = rface == 0 ? flo[0][v] : rface == 1 ? fhi[0][v] : rface == 2 ? flo[1][v] : fhi[1][v];
+                P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], val);
+            }
         }
         __syncthreads();
 

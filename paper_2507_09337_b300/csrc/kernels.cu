@@ -95,7 +95,6 @@ __global__ void signal_speed_all_kernel(const MeshDev m, const double* __restric
 // dt = cfl / max over blocks; then clear the per-block maxima for the next step.
 __global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__ dt) {
     __shared__ unsigned long long red[32];
-    __shared__ unsigned long long total;
     unsigned long long b = 0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) b = umax64(b, m.smax[i]);
     b = warp_max_u64(b);
@@ -104,7 +103,6 @@ __global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = umax64(t, red[w]);
-        total = t;
         const double s = __longlong_as_double((long long)t);
         if (s > 0.0 && s <= 1.7976931348623157e308) *dt = m.cfl / s;
         else atomicOr(m.err, 2);

@@ -72,7 +72,7 @@ extern "C" orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_
     cudaDeviceProp prop;
     e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) return orcha::cuda_error(e, "autotune: device properties");
-    char key[256];
+    char key[512];
     snprintf(key, sizeof(key), "%s|ndim=%d|bs=%dx%dx%d|task=%d", prop.name, ndim, bs[0], bs[1], ndim == 3 ? bs[2] : 1,
              (int)task);
     Cache cache = read_cache(cache_path);
