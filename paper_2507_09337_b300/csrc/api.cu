@@ -381,10 +381,12 @@ orcha_status orcha_batch_destroy(orcha_batch* b) {
     if (!b) return ORCHA_OK;
     cudaDeviceSynchronize();
     for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
-    cudaFree(b->slots_dev);
-    cudaFree(b->items_dev);
+    for (auto& l : b->lists) {
+        cudaFree(l.items_dev);
+        cudaFree(l.slots_dev);
+        cudaFree(l.done_dev);
+    }
     cudaFree(b->queue);
-    cudaFree(b->done_dev);
     cudaFree(b->cur_dev);
     delete b;
     return ORCHA_OK;
@@ -416,8 +418,6 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
             return fail(ORCHA_ERR_INVALID, "batch_create: tile %dx%d does not divide a mesh's blocks", tx, ty);
     }
     // each mesh's packets must cover its blocks exactly once (the step ends with that mesh's dt)
-    std::vector<orcha::Item> items;
-    std::vector<int> nitems(meshes.size(), 0);
     for (size_t s_ = 0; s_ < meshes.size(); ++s_) {
         orcha_mesh* m = meshes[s_];
         std::vector<char> seen((size_t)m->nblk, 0);
@@ -433,53 +433,25 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
         if (cnt != m->nblk)
             return fail(ORCHA_ERR_INVALID, "batch_create: packets cover %lld of a mesh's %d blocks", cnt, m->nblk);
     }
-    for (int i = 0; i < npk; ++i) {
-        const int slot = (int)(std::find(meshes.begin(), meshes.end(), pk[i]->mesh) - meshes.begin());
-        const orcha_mesh* m = pk[i]->mesh;
-        const int ntile = (m->dev.bs[0] / tx) * (m->dev.bs[1] / ty);
-        for (int id : pk[i]->ids)
-            for (int t = 0; t < ntile; ++t) {
-                items.push_back({slot, id, t, 0});
-                ++nitems[slot];
-            }
-    }
     orcha_batch* b = new orcha_batch();
     b->meshes = meshes;
     b->packets.assign(pk, pk + npk);
     b->ndim = ndim;
     b->tx = tx;
     b->ty = ty;
-    b->nitems = (int)items.size();
+    for (int i = 0; i < npk; ++i) {
+        const int slot = (int)(std::find(meshes.begin(), meshes.end(), pk[i]->mesh) - meshes.begin());
+        const orcha_mesh* m = pk[i]->mesh;
+        const int ntile = (m->dev.bs[0] / tx) * (m->dev.bs[1] / ty);
+        for (int id : pk[i]->ids)
+            for (int t = 0; t < ntile; ++t) b->base_items.push_back({slot, id, t, 0});
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t ns = meshes.size();
-    cudaError_t e = cudaMalloc(&b->slots_dev, sizeof(orcha::SlotDev) * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&b->items_dev, sizeof(orcha::Item) * items.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->queue, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&b->done_dev, sizeof(unsigned) * ns);
-    if (e == cudaSuccess) e = cudaMalloc(&b->cur_dev, sizeof(int) * ns);
-    if (e == cudaSuccess) e = cudaMemset(b->done_dev, 0, sizeof(unsigned) * ns);
+    cudaError_t e = cudaMalloc(&b->queue, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->cur_dev, sizeof(int) * meshes.size());
     if (e == cudaSuccess) e = orcha::configure_hydro(ndim, tx, ty);
-    if (e == cudaSuccess) {
-        std::vector<orcha::SlotDev> sl(ns);
-        for (size_t i = 0; i < ns; ++i) {
-            orcha_mesh* m = meshes[i];
-            sl[i].m = m->dev;
-            sl[i].state[0] = m->desc.state_dev[0];
-            sl[i].state[1] = m->desc.state_dev[1];
-            sl[i].dt = m->desc.dt_dev;
-            sl[i].cur = b->cur_dev + i;
-            sl[i].done = b->done_dev + i;
-            sl[i].nitems = nitems[i];
-            sl[i].nblk = m->nblk;
-            sl[i].tiles_x = m->dev.bs[0] / tx;
-            sl[i].tiles_y = m->dev.bs[1] / ty;
-        }
-        e = cudaMemcpy(b->slots_dev, sl.data(), sizeof(orcha::SlotDev) * ns, cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->items_dev, items.data(), sizeof(orcha::Item) * items.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         orcha_status st = cuda_fail(e, "batch_create");
         orcha_batch_destroy(b);
@@ -489,21 +461,74 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
     return ORCHA_OK;
 }
 
-static orcha_status batch_grid(orcha_batch* b, orcha_task task, int* grid) {
+// Work list of one precision: the full-block items, and -- when the last,
+// partial wave of resident CTAs holds at most half of them and the blocks
+// have 16 or more planes -- that wave's items split into two z halves queued
+// last, so the tail takes about half as long. Same bits either way.
+static orcha_status ensure_list(orcha_batch* b, bool f32) {
+    orcha_batch::List& L = b->lists[f32 ? 1 : 0];
+    if (L.built) return ORCHA_OK;
     int per_sm = 0;
-    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, task == ORCHA_TASK_HYDRO_F32FLUX, &per_sm),
-               "batch occupancy");
+    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, f32, &per_sm), "batch occupancy");
     if (per_sm < 1) return fail(ORCHA_ERR_UNSUPPORTED, "batch: persistent kernel does not fit on an SM");
-    *grid = std::min(b->nitems, per_sm * b->num_sms);
+    const long long G = (long long)per_sm * b->num_sms;
+    const long long N = (long long)b->base_items.size();
+    const long long R = N % G;
+    std::vector<orcha::Item> items(b->base_items);
+    if (b->ndim == 3 && R > 0 && 2 * R <= G) {
+        std::vector<orcha::Item> tail(items.end() - R, items.end());
+        items.resize((size_t)(N - R));
+        std::vector<orcha::Item> halves;
+        for (auto it : tail) {
+            const int bz = b->meshes[it.slot]->dev.bs[2];
+            if (bz >= 16) {
+                const int h = bz / 2;
+                halves.push_back({it.slot, it.blk, it.tile, 0 | (h << 8)});
+                halves.push_back({it.slot, it.blk, it.tile, h | (bz << 8)});
+            } else {
+                items.push_back(it);
+            }
+        }
+        items.insert(items.end(), halves.begin(), halves.end());
+    }
+    const size_t ns = b->meshes.size();
+    std::vector<int> per_mesh(ns, 0);
+    for (auto& it : items) ++per_mesh[it.slot];
+    std::vector<orcha::SlotDev> sl(ns);
+    cudaError_t e = cudaMalloc(&L.done_dev, sizeof(unsigned) * ns);
+    if (e == cudaSuccess) e = cudaMemset(L.done_dev, 0, sizeof(unsigned) * ns);
+    for (size_t i = 0; i < ns; ++i) {
+        orcha_mesh* m = b->meshes[i];
+        sl[i].m = m->dev;
+        sl[i].state[0] = m->desc.state_dev[0];
+        sl[i].state[1] = m->desc.state_dev[1];
+        sl[i].dt = m->desc.dt_dev;
+        sl[i].cur = b->cur_dev + i;
+        sl[i].done = L.done_dev + i;
+        sl[i].nitems = per_mesh[i];
+        sl[i].nblk = m->nblk;
+        sl[i].tiles_x = m->dev.bs[0] / b->tx;
+        sl[i].tiles_y = m->dev.bs[1] / b->ty;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&L.slots_dev, sizeof(orcha::SlotDev) * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&L.items_dev, sizeof(orcha::Item) * items.size());
+    if (e == cudaSuccess) e = cudaMemcpy(L.slots_dev, sl.data(), sizeof(orcha::SlotDev) * ns, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L.items_dev, items.data(), sizeof(orcha::Item) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch work list");
+    L.nitems = (int)items.size();
+    L.grid = (int)std::min<long long>((long long)L.nitems, G);
+    L.built = true;
     return ORCHA_OK;
 }
 
-static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, int grid, cudaStream_t st) {
+static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, cudaStream_t st) {
     const bool f32 = task == ORCHA_TASK_HYDRO_F32FLUX;
+    const orcha_batch::List& L = b->lists[f32 ? 1 : 0];
     for (int n = 0; n < nsteps; ++n) {
         ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
-        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, f32, b->slots_dev, b->items_dev, b->nitems,
-                                            b->queue, grid, st),
+        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, f32, L.slots_dev, L.items_dev, L.nitems, b->queue,
+                                            L.grid, st),
                    "batch launch");
     }
     return ORCHA_OK;
@@ -516,6 +541,7 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
         return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a hydro task");
     cudaStream_t st = (cudaStream_t)stream;
     orcha_status s;
+    if ((s = ensure_list(b, task == ORCHA_TASK_HYDRO_F32FLUX))) return s;
     if (init_dt) {
         // one launch per mesh over all its blocks (the batch covers every block)
         for (auto* m : b->meshes) {
@@ -530,10 +556,8 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
     ORCHA_CUDA(cudaMemcpyAsync(b->cur_dev, cur.data(), sizeof(int) * cur.size(), cudaMemcpyHostToDevice, st),
                "batch cur upload");
     if (nsteps == 0) return ORCHA_OK;
-    int grid = 0;
-    if ((s = batch_grid(b, task, &grid))) return s;
     if (!use_graph) {
-        if ((s = enqueue_batch_steps(b, task, nsteps, grid, st))) return s;
+        if ((s = enqueue_batch_steps(b, task, nsteps, st))) return s;
     } else {
         if (st == nullptr) return fail(ORCHA_ERR_INVALID, "batch_advance: graph capture needs a non-default stream");
         cudaGraphExec_t exec = nullptr;
@@ -541,7 +565,7 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
             if (g.task == task && g.nsteps == nsteps) exec = g.exec;
         if (!exec) {
             ORCHA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-            s = enqueue_batch_steps(b, task, nsteps, grid, st);
+            s = enqueue_batch_steps(b, task, nsteps, st);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(st, &graph);
             if (s) { if (graph) cudaGraphDestroy(graph); return s; }

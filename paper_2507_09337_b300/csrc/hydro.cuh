@@ -187,7 +187,10 @@ struct Tile {
     }
 };
 
-// One column tile of one block: the whole z sweep. Returns this thread's
+// One column tile of one block: the z sweep over interior planes [z0, z1)
+// (default: the whole block; a sub-range recomputes its own z halo, so a
+// block may be advanced as several z slabs with the same result bits).
+// Returns this thread's
 // largest signal speed of the new state (0 for threads without cells).
 // GATHER = false: guard cells are read from the padded block (filled by the
 // guard-fill task). GATHER = true: guard cells are read straight from the
@@ -197,7 +200,7 @@ struct Tile {
 template <int NDIM, int TX, int TY, class T, bool GATHER>
 __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
                                              const double* __restrict__ Uin, double* __restrict__ Uout,
-                                             unsigned char* smem_raw) {
+                                             unsigned char* smem_raw, int z0 = 0, int z1 = -1) {
     using Tl = Tile<NDIM, TX, TY>;
     using S = typename P<T>::store;
     constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
@@ -214,6 +217,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     const double* Ub = Uin + (long long)blk * m.blk_stride;
     double* Ob = Uout + (long long)blk * m.blk_stride;
     const int bz = (NDIM == 3) ? m.bs[2] : 1;
+    if (NDIM != 3 || z1 < 0) { z0 = 0; z1 = bz; }
     const int bc[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
 
     const T g = P<T>::in(m.gamma), gm1 = P<T>::in(m.gm1), igm1 = P<T>::in(m.igm1);
@@ -405,11 +409,11 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         cl[d] = F32 ? d2f_rn(__dsub_rn(cd[d], to_f64(ch[d]))) : 0.0f;
     }
 
-    const int pbeg = (NDIM == 3) ? -1 : 0, pend = (NDIM == 3) ? bz : 0;
-    if (NDIM == 3) { load_plane(-2); load_plane(-1); }
+    const int pbeg = (NDIM == 3) ? z0 - 1 : 0, pend = (NDIM == 3) ? z1 : 0;
+    if (NDIM == 3) { load_plane(z0 - 2); load_plane(z0 - 1); }
 
     for (int p = pbeg; p <= pend; ++p) {
-        const bool inner = p >= 0 && p < bz;       // plane p is interior: it has x/y faces to flux
+        const bool inner = p >= z0 && p < z1;      // plane p is updated here: it has x/y faces to flux
         if (NDIM == 3) load_plane(p + 1);
         else load_plane(0);
         __syncthreads();
@@ -486,7 +490,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             T Fz[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) Fz[v] = P<T>::zero();
-            if (p >= 0) {
+            if (p >= z0) {
                 T L[NV], R[NV];
                 L[0] = zp_prev[0]; L[1] = zp_prev[3]; L[2] = zp_prev[1]; L[3] = zp_prev[2]; L[4] = zp_prev[4];
                 R[0] = zlo[0]; R[1] = zlo[3]; R[2] = zlo[1]; R[3] = zlo[2]; R[4] = zlo[4];
@@ -494,7 +498,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 hll<T, NDIM, true>(L, R, F, g, igm1);
                 Fz[0] = F[0]; Fz[3] = F[1]; Fz[1] = F[2]; Fz[2] = F[3]; Fz[4] = F[4];
             }
-            if (p >= 1) {
+            if (p >= z0 + 1) {
                 const int q = p - 1;
                 const long long gi = ((long long)(q + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
                 rd Un[NV];

@@ -34,8 +34,10 @@ struct SlotDev {
     int tiles_x, tiles_y;
 };
 
+// One unit of work: a column tile of a block, over the interior planes
+// [z0, z1) when zr = z0 | z1 << 8 is non-zero, else over the whole block.
 struct Item {
-    int slot, blk, tile, pad;
+    int slot, blk, tile, zr;
 };
 
 // Finish a mesh's step: dt = cfl / max signal speed, clear the maxima and the
@@ -59,8 +61,15 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
     for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.m.smax[i] = 0ull;
 }
 
+// Resident CTAs per SM requested from the register allocator (A/B-measured
+// on a B300): the FP64 variant, bound by the FP64 pipe, gains from 384
+// threads per SM (a small spill; +2 %); the FP32-flux variant runs best at
+// 512 threads per SM (128 registers) and loses from the spills of more.
+template <class T, int NT> struct MinBlocks { static constexpr int value = (512 / NT) > 1 ? (512 / NT) : 1; };
+template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
+
 template <int NDIM, int TX, int TY, class T>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (MinBlocks<T, TX * TY>::value))
 persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ items, int nitems,
                   unsigned int* __restrict__ queue) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -74,9 +83,10 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         const Item w = items[it];
         const SlotDev& sd = slots[w.slot];
         const int cur = __ldcg(sd.cur);
+        const int z0 = w.zr ? (w.zr & 0xFF) : 0, z1 = w.zr ? (w.zr >> 8) : -1;
         const double s = hydro_tile<NDIM, TX, TY, T, true>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
                                                            (w.tile / sd.tiles_x) * TY, sd.state[cur],
-                                                           sd.state[cur ^ 1], smem_raw);
+                                                           sd.state[cur ^ 1], smem_raw, z0, z1);
         cta_raise_smax(s, red, &sd.m.smax[w.blk]);
         if (threadIdx.x == 0) {
             __threadfence();

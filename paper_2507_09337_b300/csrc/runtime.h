@@ -45,11 +45,16 @@ struct orcha_batch {
     std::vector<orcha_mesh*> meshes;                 // one slot per mesh
     std::vector<const orcha_packet*> packets;
     int ndim = 3, tx = 8, ty = 8;
-    int nitems = 0;
-    orcha::SlotDev* slots_dev = nullptr;
-    orcha::Item* items_dev = nullptr;
+    std::vector<orcha::Item> base_items;             // full-block items in packet order
+    // per precision (0: FP64, 1: FP32 flux): work list sized for that variant's occupancy
+    struct List {
+        bool built = false;
+        int nitems = 0, grid = 0;
+        orcha::Item* items_dev = nullptr;
+        orcha::SlotDev* slots_dev = nullptr;
+        unsigned* done_dev = nullptr;
+    } lists[2];
     unsigned* queue = nullptr;
-    unsigned* done_dev = nullptr;
     int* cur_dev = nullptr;
     int num_sms = 0;
     struct G { orcha_task task; int nsteps; cudaGraphExec_t exec; };
