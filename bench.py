@@ -145,7 +145,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- the oracle on the host cores
 
-def oracle_rate(spec, U0, seconds: float, max_steps: int = 50):
+def oracle_rate(spec, U0, seconds: float, max_steps: int = 400):
     """Zone-updates/s of the oracle on the full mesh, stepping until `seconds`
     of wall time have passed (at least one step)."""
     import oracle

@@ -76,12 +76,20 @@ template <> struct P<rd> {
                         mb <= 0x7FF0000000000000LL;
         return ok ? (ma < mb ? a : b) : rd(0.0);
     }
-    // 0.5 * x: exponent decrement when the result is normal, else the IEEE multiply
+    // 0.5 * x, entirely on the integer pipe (a fallback multiply would be
+    // predicated into every call): exponent decrement when the result is
+    // normal; infinities and NaN unchanged; otherwise the result is in the
+    // subnormal range and is the magnitude bits shifted right by one with the
+    // dropped bit rounded to nearest even (the IEEE result bit for bit).
     static __device__ __forceinline__ rd half(rd x) {
-        const long long b = bits(x);
-        const int e = (int)((b >> 52) & 0x7FF);
-        if (e > 1 && e < 0x7FF) return rd(__longlong_as_double(b - (1LL << 52)));
-        return rd(__dmul_rn(x.v, 0.5));
+        const unsigned long long b = (unsigned long long)bits(x);
+        const unsigned long long sign = b & 0x8000000000000000ull, a = b & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned e = (unsigned)(a >> 52);
+        unsigned long long r;
+        if (e > 1u && e < 0x7FFu) r = a - (1ull << 52);
+        else if (e == 0x7FFu) r = a;
+        else r = (a >> 1) + ((a & 1ull) & ((a >> 1) & 1ull));
+        return rd(__longlong_as_double((long long)(sign | r)));
     }
     static __device__ __forceinline__ rd zero() { return rd(0.0); }
     static __device__ __forceinline__ double to_double(rd x) { return x.v; }
