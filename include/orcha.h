@@ -338,6 +338,15 @@ ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* 
 ORCHA_API orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64_t count, uint64_t seed,
                                                   uint64_t* mismatches);
 
+/* Diagnostics: part of the FP64 task's adds, subtracts and multiplies are
+ * computed with integer instructions (the FP64 pipe is the bound of that
+ * task on this GPU), exactly as IEEE-754 round-to-nearest-even defines them.
+ * This checks them against the hardware instructions on `count`
+ * pseudo-random operand pairs derived from `seed` (biased toward carries,
+ * ties, cancellation and zeros); *mismatches receives the number of results
+ * whose bits differ (NaN results excepted). Synchronous. */
+ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64_t* mismatches);
+
 /* Message of the last error returned on this thread ("" if none). */
 ORCHA_API const char* orcha_last_error(void);
 

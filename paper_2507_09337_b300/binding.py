@@ -126,6 +126,7 @@ SIGNATURES = {
     "orcha_mesh_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
     "orcha_selftest_conversions": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "orcha_selftest_fp64_emulation": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
 
@@ -308,6 +309,12 @@ def orcha_mesh_poll(mesh: int, stream=None) -> int:
 def orcha_selftest_conversions(first_pattern: int, count: int, seed: int = 1) -> int:
     bad = ctypes.c_uint64()
     _check(lib().orcha_selftest_conversions(int(first_pattern), int(count), int(seed), ctypes.byref(bad)))
+    return bad.value
+
+
+def orcha_selftest_fp64_emulation(count: int, seed: int = 1) -> int:
+    bad = ctypes.c_uint64()
+    _check(lib().orcha_selftest_fp64_emulation(int(count), int(seed), ctypes.byref(bad)))
     return bad.value
 
 

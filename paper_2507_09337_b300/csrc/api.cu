@@ -608,6 +608,20 @@ orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64_t count, 
     return ORCHA_OK;
 }
 
+orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64_t* mismatches) {
+    if (!mismatches) return fail(ORCHA_ERR_INVALID, "selftest: null argument");
+    unsigned long long* bad = nullptr;
+    ORCHA_CUDA(cudaMalloc(&bad, sizeof(unsigned long long)), "selftest alloc");
+    cudaError_t e = cudaMemset(bad, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = orcha::launch_selftest_fp64(count, seed, bad, nullptr);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    *mismatches = h;
+    return ORCHA_OK;
+}
+
 const char* orcha_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

@@ -181,6 +181,47 @@ __device__ __forceinline__ double to_f64(float x) {
 #endif
 }
 
+// ---------------------------------------------------------------- FP64 on the integer pipe
+// Same values as rd (IEEE round-to-nearest-even, never fused), computed by
+// integer instructions (softfp64.cuh): the FP64 task moves a share of its
+// adds and multiplies here to balance the FP64 pipe against the idle
+// integer pipe.
+struct re {
+    double v;
+    __device__ __forceinline__ re() {}
+    __device__ __forceinline__ constexpr re(double x) : v(x) {}
+};
+}  // namespace orcha
+#include "softfp64.cuh"
+namespace orcha {
+__device__ __forceinline__ re operator+(re a, re b) { return re(em_add(a.v, b.v)); }
+__device__ __forceinline__ re operator-(re a, re b) { return re(em_sub(a.v, b.v)); }
+__device__ __forceinline__ re operator*(re a, re b) { return re(em_mul(a.v, b.v)); }
+__device__ __forceinline__ re operator-(re a) { return re(-a.v); }
+
+template <> struct P<re> {
+    using store = double;
+    static __device__ __forceinline__ re in(double x) { return re(x); }
+    static __device__ __forceinline__ re rcp(re x) { return re(__drcp_rn(x.v)); }
+    static __device__ __forceinline__ re sqrt(re x) { return re(__dsqrt_rn(x.v)); }
+    static __device__ __forceinline__ bool pos(re x) { return P<rd>::pos(rd(x.v)); }
+    static __device__ __forceinline__ bool neg(re x) { return P<rd>::neg(rd(x.v)); }
+    static __device__ __forceinline__ bool lt(re a, re b) { return P<rd>::lt(rd(a.v), rd(b.v)); }
+    static __device__ __forceinline__ bool ge0(re a) { return P<rd>::ge0(rd(a.v)); }
+    static __device__ __forceinline__ bool le0(re a) { return P<rd>::le0(rd(a.v)); }
+    static __device__ __forceinline__ re minmod(re a, re b) { return re(P<rd>::minmod(rd(a.v), rd(b.v)).v); }
+    static __device__ __forceinline__ re half(re x) { return re(P<rd>::half(rd(x.v)).v); }
+    static __device__ __forceinline__ re zero() { return re(0.0); }
+};
+
+// Value-preserving moves between the FP64 arithmetic types (free: both hold a double).
+template <class A, class T> __device__ __forceinline__ A as(T x);
+template <> __device__ __forceinline__ rd as<rd, rd>(rd x) { return x; }
+template <> __device__ __forceinline__ re as<re, rd>(rd x) { return re(x.v); }
+template <> __device__ __forceinline__ rd as<rd, re>(re x) { return rd(x.v); }
+template <> __device__ __forceinline__ re as<re, re>(re x) { return x; }
+template <> __device__ __forceinline__ float as<float, float>(float x) { return x; }
+
 template <> struct P<float> {
     using store = float;
     static __device__ __forceinline__ float in(double x) { return to_f32(x); }

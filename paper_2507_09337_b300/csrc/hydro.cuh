@@ -33,6 +33,20 @@
 
 namespace orcha {
 
+// ---------------------------------------------------------------- FP64 pipe balance
+// Which stages of the FP64 task compute their adds and multiplies on the
+// integer pipe (type re) instead of the FP64 pipe (type rd); both give the
+// same bits, so the split only moves work between pipes. Bits: 1 primitive
+// conversion on load, 2 predictor, 4 HLL left state, 8 HLL right state,
+// 16 HLL combination, 32 HLL wave speeds. Measured on a B300: every
+// emulated share is slower (an emulated operation costs more integer issue
+// than the FP64-pipe time it frees), so the default is 0.
+#ifndef ORCHA_EMU
+#define ORCHA_EMU 0
+#endif
+template <class T, int BIT>
+using Arith = typename std::conditional<std::is_same<T, rd>::value && ((ORCHA_EMU & BIT) != 0), re, T>::type;
+
 // ---------------------------------------------------------------- point functions
 
 // W from U: r = 1/rho, u_d = m_d * r, p = (gamma-1) * (E - 0.5 * sum_d m_d u_d).
@@ -51,6 +65,19 @@ __device__ __forceinline__ void prim_from_cons(const T* U, T* W, T& r, T gm1) {
     W[NV - 1] = gm1 * (U[NV - 1] - ke);
 }
 
+// The same with the arithmetic done in type A (values in and out in T).
+template <class A, class T, int NDIM>
+__device__ __forceinline__ void prim_from_cons_as(const T* U, T* W, T& r, T gm1) {
+    constexpr int NV = NDIM + 2;
+    A u[NV], w[NV], ra;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = as<A>(U[v]);
+    prim_from_cons<A, NDIM>(u, w, ra, as<A>(gm1));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v] = as<T>(w[v]);
+    r = as<T>(ra);
+}
+
 // minmod: the smaller-magnitude argument when both share a strict sign, else 0.
 template <class T>
 __device__ __forceinline__ T minmod(T a, T b) {
@@ -61,50 +88,65 @@ __device__ __forceinline__ T minmod(T a, T b) {
 // W = (rho, u_n, u_t1[, u_t2], p). |u|^2 is summed in coordinate order x, y, z;
 // for an x or y normal that is (u_n^2 + u_t1^2) + u_t2^2 (addition commutes),
 // for a z normal (u_t1^2 + u_t2^2) + u_n^2.
-template <class T, int NDIM, bool ZNORMAL>
-__device__ __forceinline__ void cons_flux(const T* W, T* U, T* F, T igm1) {
+template <class A, class T, int NDIM, bool ZNORMAL>
+__device__ __forceinline__ void cons_flux(const T* Wt, T* Ut, T* Ft, T igm1t) {
     constexpr int NV = NDIM + 2;
-    const T rho = W[0], un = W[1], p = W[NV - 1];
+    A W[NV], U[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v] = as<A>(Wt[v]);
+    const A igm1 = as<A>(igm1t);
+    const A rho = W[0], un = W[1], p = W[NV - 1];
     U[0] = rho;
 #pragma unroll
     for (int k = 1; k <= NDIM; ++k) U[k] = rho * W[k];
-    T q2;
+    A q2;
     if (NDIM == 2) q2 = (W[1] * W[1]) + (W[2] * W[2]);
     else if (!ZNORMAL) q2 = ((W[1] * W[1]) + (W[2] * W[2])) + (W[3] * W[3]);
     else q2 = ((W[2] * W[2]) + (W[3] * W[3])) + (W[1] * W[1]);
-    U[NV - 1] = (p * igm1) + (P<T>::half(rho) * q2);
+    U[NV - 1] = (p * igm1) + (P<A>::half(rho) * q2);
     F[0] = U[1];
     F[1] = (U[1] * un) + p;
 #pragma unroll
     for (int k = 2; k <= NDIM; ++k) F[k] = U[k] * un;
     F[NV - 1] = (U[NV - 1] + p) * un;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        Ut[v] = as<T>(U[v]);
+        Ft[v] = as<T>(F[v]);
+    }
 }
 
 // HLL flux with Davis wave speeds between normal-first states L and R.
 template <class T, int NDIM, bool ZNORMAL>
 __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     constexpr int NV = NDIM + 2;
-    const T cL = P<T>::sqrt((g * L[NV - 1]) * P<T>::rcp(L[0]));
-    const T cR = P<T>::sqrt((g * R[NV - 1]) * P<T>::rcp(R[0]));
-    T a = L[1] - cL, b = R[1] - cR;
-    const T SL = P<T>::lt(a, b) ? a : b;
-    a = L[1] + cL;
-    b = R[1] + cR;
-    const T SR = P<T>::lt(b, a) ? a : b;
+    using AS = Arith<T, 32>;     // wave speeds
+    using AC = Arith<T, 16>;     // combination
+    const AS gs = as<AS>(g);
+    const AS cL = P<AS>::sqrt((gs * as<AS>(L[NV - 1])) * P<AS>::rcp(as<AS>(L[0])));
+    const AS cR = P<AS>::sqrt((gs * as<AS>(R[NV - 1])) * P<AS>::rcp(as<AS>(R[0])));
+    AS a = as<AS>(L[1]) - cL, b = as<AS>(R[1]) - cR;
+    const AS SL = P<AS>::lt(a, b) ? a : b;
+    a = as<AS>(L[1]) + cL;
+    b = as<AS>(R[1]) + cR;
+    const AS SR = P<AS>::lt(b, a) ? a : b;
     T UL[NV], UR[NV], FL[NV], FR[NV];
-    cons_flux<T, NDIM, ZNORMAL>(L, UL, FL, igm1);
-    cons_flux<T, NDIM, ZNORMAL>(R, UR, FR, igm1);
-    if (P<T>::ge0(SL)) {
+    cons_flux<Arith<T, 4>, T, NDIM, ZNORMAL>(L, UL, FL, igm1);
+    cons_flux<Arith<T, 8>, T, NDIM, ZNORMAL>(R, UR, FR, igm1);
+    if (P<AS>::ge0(SL)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FL[v];
-    } else if (P<T>::le0(SR)) {
+    } else if (P<AS>::le0(SR)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FR[v];
     } else {
-        const T slsr = SL * SR;
-        const T inv = P<T>::rcp(SR - SL);
+        const AC sl = as<AC>(SL), sr = as<AC>(SR);
+        const AC slsr = sl * sr;
+        const AC inv = P<AC>::rcp(sr - sl);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) F[v] = (((SR * FL[v]) - (SL * FR[v])) + (slsr * (UR[v] - UL[v]))) * inv;
+        for (int v = 0; v < NV; ++v)
+            F[v] = as<T>((((sr * as<AC>(FL[v])) - (sl * as<AC>(FR[v]))) +
+                          (slsr * (as<AC>(UR[v]) - as<AC>(UL[v])))) * inv);
     }
 }
 
@@ -308,7 +350,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             T U[NV], W[NV], r;
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[v] = P<T>::in(src[v * vs]);
-            prim_from_cons<T, NDIM>(U, W, r, gm1);
+            prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W, r, gm1);
 #pragma unroll
             for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
             P<T>::st(&w[NV * R2N + c], r);
@@ -320,12 +362,13 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     // P: slopes, predictor and face states of the cell at R2 index c2 of plane
     // pzi; writes flo/fhi (face states on the low/high side along each axis).
     auto predict = [&](int pzi, int c2, T (&flo)[3][NV], T (&fhi)[3][NV]) {
+        using A = Arith<T, 2>;     // arithmetic type of the predictor
         const int sc = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
         const S* w = sW + sc * NW * R2N;
-        T Wc[NV], dW[3][NV], a[3][NV];
+        A Wc[NV], dW[3][NV], a[3][NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Wc[v] = P<T>::ld(&w[v * R2N + c2]);
-        const T rc = P<T>::ld(&w[NV * R2N + c2]);
+        for (int v = 0; v < NV; ++v) Wc[v] = as<A>(P<T>::ld(&w[v * R2N + c2]));
+        const A rc = as<A>(P<T>::ld(&w[NV * R2N + c2]));
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
             const S* wm;
@@ -339,27 +382,27 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const T dl = Wc[v] - P<T>::ld(&wm[v * R2N + cm]);
-                const T dr = P<T>::ld(&wp[v * R2N + cp]) - Wc[v];
+                const A dl = Wc[v] - as<A>(P<T>::ld(&wm[v * R2N + cm]));
+                const A dr = as<A>(P<T>::ld(&wp[v * R2N + cp])) - Wc[v];
                 dW[d][v] = minmod(dl, dr);
             }
         }
-        const T gp = g * Wc[NV - 1];
+        const A gp = as<A>(g) * Wc[NV - 1];
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const T un = Wc[1 + d], dun = dW[d][1 + d], dp = dW[d][NV - 1];
+            const A un = Wc[1 + d], dun = dW[d][1 + d], dp = dW[d][NV - 1];
             a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);
 #pragma unroll
             for (int t = 0; t < NDIM; ++t)
                 a[d][1 + t] = (t == d) ? ((un * dun) + (dp * rc)) : (un * dW[d][1 + t]);
             a[d][NV - 1] = (gp * dun) + (un * dp);
         }
-        T Wb[NV];
+        A Wb[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            T s = hd[0] * a[0][v];
+            A s = as<A>(hd[0]) * a[0][v];
 #pragma unroll
-            for (int d = 1; d < NDIM; ++d) s = s + (hd[d] * a[d][v]);
+            for (int d = 1; d < NDIM; ++d) s = s + (as<A>(hd[d]) * a[d][v]);
             Wb[v] = Wc[v] - s;
         }
         bool ok = true;
@@ -367,9 +410,9 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         for (int d = 0; d < NDIM; ++d) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const T hs = P<T>::half(dW[d][v]);
-                flo[d][v] = Wb[v] - hs;
-                fhi[d][v] = Wb[v] + hs;
+                const A hs = P<A>::half(dW[d][v]);
+                flo[d][v] = as<T>(Wb[v] - hs);
+                fhi[d][v] = as<T>(Wb[v] + hs);
             }
             ok = ok && P<T>::pos(flo[d][0]) && P<T>::pos(flo[d][NV - 1]) && P<T>::pos(fhi[d][0]) &&
                  P<T>::pos(fhi[d][NV - 1]);
@@ -378,7 +421,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 #pragma unroll
             for (int d = 0; d < NDIM; ++d)
 #pragma unroll
-                for (int v = 0; v < NV; ++v) { flo[d][v] = Wc[v]; fhi[d][v] = Wc[v]; }
+                for (int v = 0; v < NV; ++v) { flo[d][v] = as<T>(Wc[v]); fhi[d][v] = as<T>(Wc[v]); }
         }
     };
 

@@ -6,6 +6,7 @@
 #include "hydro.cuh"
 #include "launch.h"
 #include "persistent.cuh"
+#include "softfp64.cuh"
 
 namespace orcha {
 
@@ -265,6 +266,56 @@ __global__ void selftest_kernel(unsigned long long lo, unsigned long long n, uns
         if (__float_as_uint(x) != __float_as_uint(y) && !(x != x && y != y)) ++cnt;
     }
     if (cnt) atomicAdd(bad, cnt);
+}
+
+// em_add / em_sub / em_mul against the hardware on pseudo-random operand
+// pairs: half unrelated (any exponent, mantissas near all-ones or near zero,
+// exact zeros), half related (the second is the first with a flipped sign,
+// low mantissa bits perturbed and the exponent moved by a few), which
+// exercises carries, ties and cancellation.
+__device__ __forceinline__ unsigned long long rand_double_bits(unsigned long long z) {
+    const unsigned long long r = mix64(z), r2 = mix64(z ^ 0x5DEECE66Dull);
+    const unsigned k = (unsigned)(r2 % 6);
+    const unsigned long long sign = (r2 >> 8) & 1ull;
+    if (k == 0) return r;
+    if (k == 5) return sign << 63;                                   // +-0
+    const unsigned long long e = (k == 1) ? 1 + (r2 >> 16) % 2046 : 1000 + (r2 >> 16) % 50;
+    unsigned long long m = r & kM52;
+    if (k == 3) m = kM52 - ((r2 >> 32) & 15);
+    if (k == 4) m = (r2 >> 32) & 15;
+    return (sign << 63) | (e << 52) | m;
+}
+
+__global__ void selftest_fp64_kernel(unsigned long long n, unsigned long long seed, unsigned long long* bad) {
+    unsigned long long cnt = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = rand_double_bits(seed + 2 * i);
+        unsigned long long b;
+        const unsigned long long r = mix64(seed ^ (i * 0x9E3779B97F4A7C15ull));
+        if (r & 1) {
+            b = a ^ ((r >> 1) & 1ull) << 63;
+            b ^= (r >> 2) & ((1ull << (1 + (r >> 58) % 52)) - 1ull);
+            const long long e = (long long)((b >> 52) & 0x7FF) + (long long)((r >> 40) % 7) - 3;
+            if (e > 0 && e < 0x7FF) b = (b & ~(0x7FFull << 52)) | ((unsigned long long)e << 52);
+        } else {
+            b = rand_double_bits(seed + 2 * i + 1);
+        }
+        const double x = __longlong_as_double((long long)a), y = __longlong_as_double((long long)b);
+        const double m1 = em_mul(x, y), m2 = __dmul_rn(x, y);
+        const double a1 = em_add(x, y), a2 = __dadd_rn(x, y);
+        const double s1 = em_sub(x, y), s2 = __dsub_rn(x, y);
+        cnt += (__double_as_longlong(m1) != __double_as_longlong(m2)) && !(m2 != m2);
+        cnt += (__double_as_longlong(a1) != __double_as_longlong(a2)) && !(a2 != a2);
+        cnt += (__double_as_longlong(s1) != __double_as_longlong(s2)) && !(s2 != s2);
+    }
+    if (cnt) atomicAdd(bad, cnt);
+}
+
+cudaError_t launch_selftest_fp64(unsigned long long n, unsigned long long seed, unsigned long long* bad,
+                                 cudaStream_t st) {
+    selftest_fp64_kernel<<<148 * 16, 256, 0, st>>>(n, seed, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigned long long seed,

@@ -42,6 +42,9 @@ cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st)
 // Self-test of the integer-pipe format conversions (counts mismatches into *bad).
 cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigned long long seed,
                             unsigned long long* bad, cudaStream_t st);
+// Self-test of the integer-pipe binary64 add/sub/mul (counts mismatches into *bad).
+cudaError_t launch_selftest_fp64(unsigned long long n, unsigned long long seed, unsigned long long* bad,
+                                 cudaStream_t st);
 // Built column-tile variants, widest first.
 constexpr int kTiles[3][2] = {{16, 16}, {16, 8}, {8, 8}};
 // One persistent launch (one time step of every mesh in `slots`).

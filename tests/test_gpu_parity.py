@@ -202,3 +202,9 @@ def test_c4_f32flux_100_steps_error_against_fp64_oracle(oracle_mod):
     for v in (0, 4):
         s0, s1 = U0[:, v].sum(), G[:, v].sum()
         assert abs(s1 - s0) <= 1e-13 * abs(s0)
+
+
+def test_integer_pipe_fp64_arithmetic_matches_hardware():
+    """The integer-pipe binary64 add/sub/mul give the hardware's bits on 2^31
+    pseudo-random operand pairs (carries, ties, cancellation, zeros)."""
+    assert B.orcha_selftest_fp64_emulation(1 << 31, seed=2024) == 0
