@@ -41,7 +41,6 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr size_t kAlign = 256;
-constexpr int kTile = 8;          // 8x8 column tiles: divide every built block size
 constexpr int kInflight = 2;      // persistent steps queued ahead of the device
 
 size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
@@ -107,13 +106,21 @@ struct Req {
     double* totals = nullptr;
     double* partial = nullptr;       // nblk x 5 doubles: per-block sums of the totals reduction
     int cur_host = 0, steps_left = 0, nitems = 0, err_slot = -1;
+    int tx = 8, ty = 8;              // column tile of the hydro launch this request joins
     bool f32 = false;
     cudaEvent_t ev = nullptr;        // admission done / completion landed
     RS st = RS::Pending;
     orcha_request_stats stats{};
 };
 
-constexpr int kGroups = 4;        // (ndim 2 or 3) x (FP64 or FP32 flux): one launch each
+// One launch per (ndim 2 or 3) x (FP64 or FP32 flux) x (tile 8x8 or 16x8):
+// blocks of 16 or more cells across x use the 16x8 tile (the autotuner's
+// choice for 16^3 blocks on a B300), 8-cell blocks the 8x8 one.
+constexpr int kGroups = 8;
+__host__ __device__ constexpr int group_ndim(int g) { return 2 + ((g >> 1) & 1); }
+__host__ __device__ constexpr int group_f32(int g) { return g & 1; }
+__host__ __device__ constexpr int group_tx(int g) { return (g >> 2) ? 16 : 8; }
+constexpr int group_of(int ndim, bool f32, int tx) { return (tx == 16 ? 4 : 0) | ((ndim - 2) << 1) | (f32 ? 1 : 0); }
 
 struct GroupBuf {                    // host/device work list of one launch
     std::vector<orcha::SlotDev> slots_h;
@@ -243,13 +250,13 @@ bool orcha_server::launch_step(bool* launched) {
     }
     std::vector<Req*> finished;
     for (int gi = 0; gi < kGroups; ++gi) {
-        const int ndim = 2 + (gi >> 1), f32 = gi & 1;
+        const int ndim = group_ndim(gi), f32 = group_f32(gi), gtx = group_tx(gi), gty = 8;
         GroupBuf& g = s.g[gi];
         g.slots_h.clear();
         g.items_h.clear();
         std::vector<Req*> grp;
         for (Req* r : active)
-            if (r->m.ndim == ndim && (int)r->f32 == f32) grp.push_back(r);
+            if (group_of(r->m.ndim, r->f32, r->tx) == gi) grp.push_back(r);
         if (grp.empty()) continue;
         for (size_t i = 0; i < grp.size(); ++i) {
             Req* r = grp[i];
@@ -262,8 +269,8 @@ bool orcha_server::launch_step(bool* launched) {
             sd.done = r->done;
             sd.nitems = r->nitems;
             sd.nblk = (int)r->nblk;
-            sd.tiles_x = r->m.bs[0] / kTile;
-            sd.tiles_y = r->m.bs[1] / kTile;
+            sd.tiles_x = r->m.bs[0] / gtx;
+            sd.tiles_y = r->m.bs[1] / gty;
             g.slots_h.push_back(sd);
             const int nt = sd.tiles_x * sd.tiles_y;
             for (int b = 0; b < (int)r->nblk; ++b)
@@ -291,7 +298,7 @@ bool orcha_server::launch_step(bool* launched) {
                                  cudaMemcpyHostToDevice, compute), "step upload");
         SRV_CUDA(cudaMemsetAsync(g.queue_d, 0, sizeof(unsigned), compute), "step queue");
         const int grid = std::max(1, std::min((int)g.items_h.size(), occ[gi] * num_sms));
-        SRV_CUDA(orcha::launch_persistent(ndim, kTile, kTile, f32, g.slots_d, g.items_d, (int)g.items_h.size(),
+        SRV_CUDA(orcha::launch_persistent(ndim, gtx, gty, f32, g.slots_d, g.items_d, (int)g.items_h.size(),
                                           g.queue_d, grid, compute), "step launch");
         for (Req* r : grp) {
             r->cur_host ^= 1;
@@ -422,9 +429,12 @@ orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, or
     if (e == cudaSuccess) e = cudaMallocHost(&s->res_pin, sizeof(orcha_server::Result) * (size_t)max_active);
     for (int i = 0; e == cudaSuccess && i < kInflight; ++i)
         e = cudaEventCreateWithFlags(&s->ring[i].ev, cudaEventDisableTiming);
-    for (int nd = 2; e == cudaSuccess && nd <= 3; ++nd) e = orcha::configure_hydro(nd, kTile, kTile);
+    for (int nd = 2; e == cudaSuccess && nd <= 3; ++nd) {
+        e = orcha::configure_hydro(nd, 8, 8);
+        if (e == cudaSuccess) e = orcha::configure_hydro(nd, 16, 8);
+    }
     for (int gi = 0; e == cudaSuccess && gi < kGroups; ++gi)
-        e = orcha::persistent_occupancy(2 + (gi >> 1), kTile, kTile, gi & 1, &s->occ[gi]);
+        e = orcha::persistent_occupancy(group_ndim(gi), group_tx(gi), 8, group_f32(gi), &s->occ[gi]);
     if (e != cudaSuccess) {
         orcha_status st = orcha::cuda_error(e, "server_create");
         s->stop = true;
@@ -505,7 +515,9 @@ orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, 
     r->bytes = 2 * round_up(r->state_elems * sizeof(double)) + round_up(r->nblk * sizeof(unsigned long long)) +
                5 * kAlign + round_up(r->nblk * 5 * sizeof(double));
     r->steps_left = rd->nsteps;
-    r->nitems = (int)r->nblk * (rd->bs[0] / kTile) * (rd->bs[1] / kTile);
+    r->tx = rd->bs[0] >= 16 ? 16 : 8;
+    r->ty = 8;
+    r->nitems = (int)r->nblk * (rd->bs[0] / r->tx) * (rd->bs[1] / r->ty);
     r->stats.zone_updates = (int64_t)r->nblk * r->ncell * rd->nsteps;
     if (r->bytes > s->pool.size) {
         delete r;

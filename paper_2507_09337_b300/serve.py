@@ -16,7 +16,6 @@ hydro and dt launches) and is timed the same way.
 from __future__ import annotations
 
 import argparse
-import ctypes
 import json
 import time
 
@@ -153,23 +152,30 @@ def main():
     from . import build
     build.build()
     task = B.TASKS[args.task]
-    lines = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        stream = wl.serving_stream(args.requests, rate, max_blocks=args.max_blocks, nsteps=args.nsteps)
-        res = run_server(stream, task, int(args.budget_gb * 1e9))
-        res.pop("totals")
-        res.update(rate_per_s=rate, task=args.task, budget_gb=args.budget_gb, max_blocks=args.max_blocks)
-        lines.append(res)
-        print(json.dumps(res), flush=True)
-        if args.plain:
-            p = run_plain(stream, task)
-            p.update(rate_per_s=rate, task=args.task, max_blocks=args.max_blocks)
-            lines.append(p)
-            print(json.dumps(p), flush=True)
-    if args.out:
-        with open(args.out, "w") as f:
-            for l in lines:
-                f.write(json.dumps(l) + "\n")
+    out = open(args.out, "w") if args.out else None
+
+    def emit(res):
+        line = json.dumps(res)
+        print(line, flush=True)
+        if out:
+            out.write(line + "\n")
+            out.flush()
+
+    base = wl.serving_stream(args.requests, 1.0, max_blocks=args.max_blocks, nsteps=args.nsteps)
+    try:
+        for rate in [float(r) for r in args.rates.split(",")]:
+            stream = [(t / rate, req) for t, req in base]
+            res = run_server(stream, task, int(args.budget_gb * 1e9))
+            res.pop("totals")
+            res.update(rate_per_s=rate, task=args.task, budget_gb=args.budget_gb, max_blocks=args.max_blocks)
+            emit(res)
+            if args.plain:
+                p = run_plain(stream, task)
+                p.update(rate_per_s=rate, task=args.task, max_blocks=args.max_blocks)
+                emit(p)
+    finally:
+        if out:
+            out.close()
 
 
 if __name__ == "__main__":

@@ -329,6 +329,20 @@ def region_mask(spec: MeshSpec, kind: int, region) -> np.ndarray:
     return g[int(region[0])] < int(region[1])
 
 
+def sphere_count(spec: MeshSpec, region) -> int:
+    """Number of cells inside a sphere region (same rule as region_mask, kind
+    1), counted over the window of cells the sphere can reach."""
+    r = int(np.floor(np.sqrt(region[3]))) + 1
+    ax = []
+    for d in range(spec.ndim):
+        lo = max(0, (int(region[d]) - 1 - r) // 2 - 1)
+        hi = min(spec.ncells[d], (int(region[d]) - 1 + r) // 2 + 2)
+        ax.append(np.arange(lo, hi, dtype=np.int64))
+    g = np.meshgrid(*ax, indexing="ij")
+    d2 = sum((2 * g[d] + 1 - int(region[d])) ** 2 for d in range(spec.ndim))
+    return int((d2 <= int(region[3])).sum())
+
+
 def region_state(spec: MeshSpec, kind: int, region, u_in, u_out) -> np.ndarray:
     """Block array of a two-region initial state (same values as the device recipe)."""
     mask = region_mask(spec, kind, region)
@@ -360,7 +374,7 @@ def serving_request(rng: np.random.Generator, max_blocks: int = 512, sizes=(8, 1
         c2 = [int(rng.integers(2, 2 * n - 1)) for n in ncell]
         r2 = 49                         # radius 3.5 cells
         region = (c2[0], c2[1], c2[2], r2)
-        ndep = int(region_mask(spec, kind, region).sum())
+        ndep = sphere_count(spec, region)
         energy = float(rng.uniform(0.5, 2.0))
         dV = spec.dx(0) ** 3
         p0 = 1e-5
@@ -379,8 +393,9 @@ def serving_request(rng: np.random.Generator, max_blocks: int = 512, sizes=(8, 1
 
 def serving_stream(n: int, rate: float, seed_arrivals: int = 1, seed_requests: int = 2, **kw):
     """n requests with exponential inter-arrival times of mean 1/rate (seconds)
-    and request parameters from serving_request."""
+    and request parameters from serving_request. For one seed the request
+    sequence is the same at every rate and the arrival times scale as 1/rate."""
     ra = np.random.default_rng(seed_arrivals)
     rr = np.random.default_rng(seed_requests)
-    t = np.cumsum(ra.exponential(1.0 / rate, size=n))
+    t = np.cumsum(ra.exponential(1.0, size=n)) / rate
     return [(float(t[i]), serving_request(rr, **kw)) for i in range(n)]

@@ -466,3 +466,15 @@ def test_first_order_fallback_is_conservative_and_symmetric(oracle_mod):
         Um, _, nfm = oracle_mod.step(m, wl.mirror(spec, U0, axis), dt)
         assert nfm == nfirst
         assert np.array_equal(wl.mirror(spec, U, axis), Um)
+
+
+def test_serving_sphere_count_matches_full_mask():
+    """The windowed deposit count of the serving recipes equals the count of
+    the full-mesh mask (the initial states use it for the energy per cell)."""
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        req = wl.serving_request(rng, max_blocks=12, sizes=(8,))
+        if req["kind"] != 1:
+            continue
+        assert wl.sphere_count(req["spec"], req["region"]) == int(
+            wl.region_mask(req["spec"], 1, req["region"]).sum())
