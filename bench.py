@@ -43,9 +43,10 @@ KERNEL_SOURCES = ["paper_2507_09337_b300/csrc/common.cuh", "paper_2507_09337_b30
                   "paper_2507_09337_b300/csrc/persistent.cuh"]
 
 
-def profiled_traffic(profile_md: str):
+def profiled_traffic(profile_md: str, kernel: str):
     """DRAM bytes per launch from a committed ncu summary, or None if the
-    kernel sources changed since that capture (hash mismatch)."""
+    summary covers another kernel variant or the kernel sources changed since
+    that capture (hash mismatch)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", profile_md)
     if not os.path.exists(path):
@@ -58,7 +59,7 @@ def profiled_traffic(profile_md: str):
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
-    if fields.get("kernel_source_sha256") != h.hexdigest():
+    if fields.get("kernel_source_sha256") != h.hexdigest() or fields.get("kernel") != kernel:
         return None
     return float(fields["traffic_bytes_per_launch"])
 
@@ -300,18 +301,22 @@ def main():
     fp64_bound = task_name == "fp64"
     if fp64_bound:
         achieved = FLOPS_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e12
-        traffic = (profiled_traffic("persistent_kernel_fp64_sedov128.md")
-                   if args.workload == "sedov128" and tuple(tile[:2]) == (16, 16) else None)
+        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},rd>"
+        traffic = (profiled_traffic("persistent_kernel_fp64_sedov128.md", kname)
+                   if args.workload == "sedov128" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": f"persistent_kernel<3,{tile[0]},{tile[1]},rd>", "per_launch": "one time step of all packets",
+                "kernel": kname, "per_launch": "one time step of all packets",
                 "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
     else:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
         achieved = BYTES_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e9
+        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},float>"
+        traffic = (profiled_traffic("persistent_kernel_f32flux_sedov128.md", kname)
+                   if args.workload == "sedov128_f32" else None)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": f"persistent_kernel<3,{tile[0]},{tile[1]},float>"}
+                "traffic": traffic, "kernel": kname}
     hbm_peak = 6489.3
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]

@@ -1,11 +1,15 @@
 // common.cuh -- device-side types shared by the block-hydro kernels.
 //
-// Arithmetic contract of the FP64 path: every operation is one IEEE-754
-// round-to-nearest operation and none is fused or reordered, so a kernel
-// that evaluates the same expression tree as the scheme's definition gets
-// the same bits. The `rd` type enforces this through the __d*_rn intrinsics,
-// which the compiler never contracts into FMAs. The FP32 flux path uses
-// plain float, where contraction is allowed.
+// Arithmetic contract of the FP64 path (type rd). Default build
+// (ORCHA_FP64_CONTRACT = 1): IEEE-754 double operations that the compiler may
+// contract into FMAs, plus two rewrites that need fewer FP64-pipe slots (the
+// HLL sound speed as x * rsqrt(x * rho), the predictor as an FMA chain); the
+// result differs from the unfused definition by rounding only (a few ulp
+// per step). Exact build (ORCHA_FP64_CONTRACT = 0): every operation is one
+// round-to-nearest operation, none fused or reordered, through the __d*_rn
+// intrinsics, so the kernels evaluate the definition's expression trees and
+// reproduce an unfused CPU evaluation of them bit for bit. The FP32 flux path
+// uses plain float, where contraction is allowed.
 #pragma once
 
 #include <cstdint>
@@ -21,9 +25,19 @@ struct rd {
     __device__ __forceinline__ rd() {}
     __device__ __forceinline__ constexpr rd(double x) : v(x) {}
 };
+#ifndef ORCHA_FP64_CONTRACT
+#define ORCHA_FP64_CONTRACT 1
+#endif
+constexpr bool kContract = ORCHA_FP64_CONTRACT != 0;
+#if ORCHA_FP64_CONTRACT
+__device__ __forceinline__ rd operator+(rd a, rd b) { return rd(a.v + b.v); }
+__device__ __forceinline__ rd operator-(rd a, rd b) { return rd(a.v - b.v); }
+__device__ __forceinline__ rd operator*(rd a, rd b) { return rd(a.v * b.v); }
+#else
 __device__ __forceinline__ rd operator+(rd a, rd b) { return rd(__dadd_rn(a.v, b.v)); }
 __device__ __forceinline__ rd operator-(rd a, rd b) { return rd(__dsub_rn(a.v, b.v)); }
 __device__ __forceinline__ rd operator*(rd a, rd b) { return rd(__dmul_rn(a.v, b.v)); }
+#endif
 __device__ __forceinline__ rd operator-(rd a) { return rd(-a.v); }
 __device__ __forceinline__ bool operator<(rd a, rd b) { return a.v < b.v; }
 __device__ __forceinline__ bool operator>(rd a, rd b) { return a.v > b.v; }
@@ -53,6 +67,13 @@ template <> struct P<rd> {
     static __device__ __forceinline__ double out(rd x) { return x.v; }
     static __device__ __forceinline__ rd rcp(rd x) { return rd(__drcp_rn(x.v)); }
     static __device__ __forceinline__ rd sqrt(rd x) { return rd(__dsqrt_rn(x.v)); }
+    // sqrt(x / rho) for x = gamma * p: the definition's sqrt(x * (1/rho)), or in
+    // the contracted build x * rsqrt(x * rho) (one reciprocal square root
+    // instead of a reciprocal and a square root; rsqrt is within 1 ulp).
+    static __device__ __forceinline__ rd sound(rd x, rd rho) {
+        if constexpr (kContract) return rd(x.v * ::rsqrt(x.v * rho.v));
+        else return rd(__dsqrt_rn(__dmul_rn(x.v, __drcp_rn(rho.v))));
+    }
     static __device__ __forceinline__ rd ld(const double* p) { return rd(*p); }
     static __device__ __forceinline__ void st(double* p, rd x) { *p = x.v; }
     // x > 0 (false for +-0 and NaN; true for +inf)
@@ -204,6 +225,7 @@ template <> struct P<re> {
     static __device__ __forceinline__ re in(double x) { return re(x); }
     static __device__ __forceinline__ re rcp(re x) { return re(__drcp_rn(x.v)); }
     static __device__ __forceinline__ re sqrt(re x) { return re(__dsqrt_rn(x.v)); }
+    static __device__ __forceinline__ re sound(re x, re rho) { return re(__dsqrt_rn(em_mul(x.v, __drcp_rn(rho.v)))); }
     static __device__ __forceinline__ bool pos(re x) { return P<rd>::pos(rd(x.v)); }
     static __device__ __forceinline__ bool neg(re x) { return P<rd>::neg(rd(x.v)); }
     static __device__ __forceinline__ bool lt(re a, re b) { return P<rd>::lt(rd(a.v), rd(b.v)); }
@@ -229,6 +251,7 @@ template <> struct P<float> {
     // hardware approximations (about 1 ulp): the FP32 flux path states its error against FP64
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
     static __device__ __forceinline__ float sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    static __device__ __forceinline__ float sound(float x, float rho) { return x > 0.0f ? x * rsqrtf(x * rho) : 0.0f; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float x) { *p = x; }
     static __device__ __forceinline__ bool pos(float x) { return x > 0.0f; }

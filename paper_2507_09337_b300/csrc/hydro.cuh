@@ -10,7 +10,8 @@
 // of U+ (the next CFL time step). The paper's solver paragraph (section
 // "Experiments") describes the task only as explicit finite volume with
 // guard-cell halos refreshed before it runs; the expression trees below are
-// the ones of the FP64 definition, operation for operation.
+// the ones of the FP64 definition, operation for operation (the contracted
+// FP64 build fuses multiply-adds and rewrites two of them; see common.cuh).
 //
 // GPU mapping. One CTA owns a TX x TY column tile of one block and sweeps it
 // along z (2.5D blocking), one thread per interior column. Per plane:
@@ -123,8 +124,8 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     using AS = Arith<T, 32>;     // wave speeds
     using AC = Arith<T, 16>;     // combination
     const AS gs = as<AS>(g);
-    const AS cL = P<AS>::sqrt((gs * as<AS>(L[NV - 1])) * P<AS>::rcp(as<AS>(L[0])));
-    const AS cR = P<AS>::sqrt((gs * as<AS>(R[NV - 1])) * P<AS>::rcp(as<AS>(R[0])));
+    const AS cL = P<AS>::sound(gs * as<AS>(L[NV - 1]), as<AS>(L[0]));
+    const AS cR = P<AS>::sound(gs * as<AS>(R[NV - 1]), as<AS>(R[0]));
     AS a = as<AS>(L[1]) - cL, b = as<AS>(R[1]) - cR;
     const AS SL = P<AS>::lt(a, b) ? a : b;
     a = as<AS>(L[1]) + cL;
@@ -400,10 +401,17 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         A Wb[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            A s = as<A>(hd[0]) * a[0][v];
+            if constexpr (kContract && std::is_same<A, rd>::value) {
+                // Wc - sum_d hd_d a_d as a chain of fused multiply-subtracts
+                Wb[v] = Wc[v];
 #pragma unroll
-            for (int d = 1; d < NDIM; ++d) s = s + (as<A>(hd[d]) * a[d][v]);
-            Wb[v] = Wc[v] - s;
+                for (int d = 0; d < NDIM; ++d) Wb[v] = rd(fma(-hd[d].v, a[d][v].v, Wb[v].v));
+            } else {
+                A s = as<A>(hd[0]) * a[0][v];
+#pragma unroll
+                for (int d = 1; d < NDIM; ++d) s = s + (as<A>(hd[d]) * a[d][v]);
+                Wb[v] = Wc[v] - s;
+            }
         }
         bool ok = true;
 #pragma unroll
