@@ -8,7 +8,8 @@ per time step guard fill + hydro task on every packet + dt reduction, and
 unpack the result. Metric: zone-updates/s (interior cells x time steps / s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov128|sedov256_uneven|sedov128_f32] [--no-cpu-baseline]
+                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff]
+                    [--no-cpu-baseline]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
 of the workload (the path has no exchange step between replicas); `value` is
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sedov128",
-                    choices=["sedov128", "sedov128_f32", "sedov256_uneven"])
+                    choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -79,7 +80,7 @@ def parse():
 
 def workload(name):
     from paper_2507_09337_b300 import workloads as wl
-    if name in ("sedov128", "sedov128_f32"):
+    if name.startswith("sedov128"):
         spec, packets = wl.sedov128_packets(64)
         desc = "3D Sedov 128^3, 512 blocks of 16^3 + 2 guards, packets of 64, 10 steps"
         nt = 10
@@ -87,8 +88,13 @@ def workload(name):
         spec, packets = wl.sedov256_uneven_packets(0)
         desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
         nt = 10
-    task = "f32flux" if name.endswith("_f32") else "fp64"
+    task = "f32flux" if name.endswith("_f32") else "ff" if name.endswith("_ff") else "fp64"
     return spec, packets, nt, task, desc
+
+
+DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 update",
+          "ff": "double-word f32x2 reconstruction/flux + f64 update"}
+KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw"}
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -312,9 +318,10 @@ def main():
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
         achieved = BYTES_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e9
-        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},float>"
-        traffic = (profiled_traffic("persistent_kernel_f32flux_sedov128.md", kname)
-                   if args.workload == "sedov128_f32" else None)
+        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
+        prof = {"sedov128_f32": "persistent_kernel_f32flux_sedov128.md",
+                "sedov128_ff": "persistent_kernel_ff_sedov128.md"}.get(args.workload)
+        traffic = profiled_traffic(prof, kname) if prof else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": kname}
     hbm_peak = 6489.3
@@ -358,7 +365,7 @@ def main():
     line = {
         "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[task_name], "data": "synthetic",
         "config": {"workload": desc, "task": task_name, "zones_per_step": spec.zones * nt,
                    "tile": f"{tile[0]}x{tile[1]} (autotuned, {tile[2]:.3f} ms/step on the tuning mesh)",
                    "l2": "inputs larger than L2 (two 164 MB state buffers + 84 MB initial state)",

@@ -97,7 +97,14 @@ typedef enum {
     ORCHA_TASK_HYDRO_F32FLUX = 2,
     /* Only the blocks' largest signal speed of the current buffer (to form
      * the first time step). */
-    ORCHA_TASK_SIGNAL_SPEED = 3
+    ORCHA_TASK_SIGNAL_SPEED = 3,
+    /* As HYDRO_FP64 with primitives, reconstruction, predictor and HLL fluxes
+     * in double-word ("float-float") arithmetic: each value a pair of FP32
+     * numbers, about 48 significant bits, on the FP32 pipe. The flux
+     * differences are double-word, the conservative update, the guard fill
+     * and the dt reduction FP64. Not in the paper: a variant of its task
+     * for a GPU whose FP64 rate is a small fraction of its FP32 rate. */
+    ORCHA_TASK_HYDRO_FF = 4
 } orcha_task;
 
 /* Mesh geometry and the caller's device buffers. */
@@ -240,7 +247,7 @@ typedef struct orcha_request_desc {
     int32_t ndim, nb[3], bs[3], periodic[3]; /* as in orcha_mesh_desc */
     double gamma, cfl, lo[3], hi[3];
     int32_t nsteps;           /* time steps to advance (>= 1); the first dt comes from the initial state */
-    int32_t task;             /* ORCHA_TASK_HYDRO_FP64 or ORCHA_TASK_HYDRO_F32FLUX */
+    int32_t task;             /* ORCHA_TASK_HYDRO_FP64, _F32FLUX or _FF */
     int32_t init_kind;        /* ORCHA_INIT_* */
     int32_t region[4];
     double u_in[5], u_out[5]; /* conserved states (rho, m_x, m_y[, m_z], E) of the recipes */
@@ -346,6 +353,16 @@ ORCHA_API orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64
  * ties, cancellation and zeros); *mismatches receives the number of results
  * whose bits differ (NaN results excepted). Synchronous. */
 ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64_t* mismatches);
+
+/* Diagnostics: the FF task computes in double-word arithmetic (pairs of
+ * binary32 numbers). This measures its building blocks against FP64
+ * references on `count` pseudo-random operands derived from `seed`
+ * (magnitudes 2^-30 .. 2^30, both signs, half of the sum operands nearly
+ * cancelling) and writes the largest errors to max_err: [0] binary64 ->
+ * double-word (relative), [1] sum (relative to |x| + |y|), [2] product,
+ * [3] reciprocal, [4] reciprocal square root, [5] sound speed
+ * sqrt(x / rho) (relative). Synchronous. Errors: INVALID, CUDA. */
+ORCHA_API orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, double max_err[6]);
 
 /* Message of the last error returned on this thread ("" if none). */
 ORCHA_API const char* orcha_last_error(void);

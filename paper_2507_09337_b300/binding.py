@@ -33,12 +33,13 @@ ORCHA_TASK_GUARD_FILL = 0
 ORCHA_TASK_HYDRO_FP64 = 1
 ORCHA_TASK_HYDRO_F32FLUX = 2
 ORCHA_TASK_SIGNAL_SPEED = 3
+ORCHA_TASK_HYDRO_FF = 4
 
 ORCHA_INIT_FROM_HOST = 0
 ORCHA_INIT_SPHERE = 1
 ORCHA_INIT_HALF_SPACE = 2
 
-TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX}
+TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF}
 
 
 class OrchaError(RuntimeError):
@@ -127,6 +128,7 @@ SIGNATURES = {
     "orcha_selftest_conversions": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_fp64_emulation": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "orcha_selftest_dword": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
 
@@ -316,6 +318,12 @@ def orcha_selftest_fp64_emulation(count: int, seed: int = 1) -> int:
     bad = ctypes.c_uint64()
     _check(lib().orcha_selftest_fp64_emulation(int(count), int(seed), ctypes.byref(bad)))
     return bad.value
+
+
+def orcha_selftest_dword(count: int, seed: int = 1) -> list:
+    err = (ctypes.c_double * 6)()
+    _check(lib().orcha_selftest_dword(int(count), int(seed), err))
+    return list(err)
 
 
 def orcha_last_error() -> str:

@@ -291,8 +291,8 @@ orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
         case ORCHA_TASK_GUARD_FILL: e = orcha::launch_guard_fill(m->dev, p->ids_dev, p->n, cur, st); break;
         case ORCHA_TASK_HYDRO_FP64:
         case ORCHA_TASK_HYDRO_F32FLUX:
-            e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, task == ORCHA_TASK_HYDRO_F32FLUX, p->ids_dev, p->n,
-                                    cur, nxt, st);
+        case ORCHA_TASK_HYDRO_FF:
+            e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, orcha::prec_of(task), p->ids_dev, p->n, cur, nxt, st);
             break;
         case ORCHA_TASK_SIGNAL_SPEED: e = orcha::launch_signal_speed(m->dev, p->ids_dev, p->n, cur, st); break;
         default: return fail(ORCHA_ERR_INVALID, "packet_run: unknown task %d", (int)task);
@@ -331,7 +331,7 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
 orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t npk, orcha_task task, int32_t nsteps,
                                 int32_t init_dt, int32_t use_graph, void* stream) {
     if (!m || (!pk && npk > 0) || npk < 0 || nsteps < 0) return fail(ORCHA_ERR_INVALID, "mesh_advance: bad argument");
-    if (task != ORCHA_TASK_HYDRO_FP64 && task != ORCHA_TASK_HYDRO_F32FLUX)
+    if (orcha::prec_of(task) < 0)
         return fail(ORCHA_ERR_INVALID, "mesh_advance: task must be a hydro task");
     long long covered = 0;
     for (int i = 0; i < npk; ++i) {
@@ -465,11 +465,11 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
 // partial wave of resident CTAs holds at most half of them and the blocks
 // have 16 or more planes -- that wave's items split into two z halves queued
 // last, so the tail takes about half as long. Same bits either way.
-static orcha_status ensure_list(orcha_batch* b, bool f32) {
-    orcha_batch::List& L = b->lists[f32 ? 1 : 0];
+static orcha_status ensure_list(orcha_batch* b, int prec) {
+    orcha_batch::List& L = b->lists[prec];
     if (L.built) return ORCHA_OK;
     int per_sm = 0;
-    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, f32, &per_sm), "batch occupancy");
+    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, prec, &per_sm), "batch occupancy");
     if (per_sm < 1) return fail(ORCHA_ERR_UNSUPPORTED, "batch: persistent kernel does not fit on an SM");
     const long long G = (long long)per_sm * b->num_sms;
     const long long N = (long long)b->base_items.size();
@@ -523,11 +523,11 @@ static orcha_status ensure_list(orcha_batch* b, bool f32) {
 }
 
 static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, cudaStream_t st) {
-    const bool f32 = task == ORCHA_TASK_HYDRO_F32FLUX;
-    const orcha_batch::List& L = b->lists[f32 ? 1 : 0];
+    const int prec = orcha::prec_of(task);
+    const orcha_batch::List& L = b->lists[prec];
     for (int n = 0; n < nsteps; ++n) {
         ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
-        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, f32, L.slots_dev, L.items_dev, L.nitems, b->queue,
+        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, prec, L.slots_dev, L.items_dev, L.nitems, b->queue,
                                             L.grid, st),
                    "batch launch");
     }
@@ -537,11 +537,11 @@ static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nst
 orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps, int32_t init_dt, int32_t use_graph,
                                  void* stream) {
     if (!b || nsteps < 0) return fail(ORCHA_ERR_INVALID, "batch_advance: bad argument");
-    if (task != ORCHA_TASK_HYDRO_FP64 && task != ORCHA_TASK_HYDRO_F32FLUX)
+    if (orcha::prec_of(task) < 0)
         return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a hydro task");
     cudaStream_t st = (cudaStream_t)stream;
     orcha_status s;
-    if ((s = ensure_list(b, task == ORCHA_TASK_HYDRO_F32FLUX))) return s;
+    if ((s = ensure_list(b, orcha::prec_of(task)))) return s;
     if (init_dt) {
         // one launch per mesh over all its blocks (the batch covers every block)
         for (auto* m : b->meshes) {
@@ -619,6 +619,20 @@ orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64
     cudaFree(bad);
     if (e != cudaSuccess) return cuda_fail(e, "selftest");
     *mismatches = h;
+    return ORCHA_OK;
+}
+
+orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, double max_err[6]) {
+    if (!max_err) return fail(ORCHA_ERR_INVALID, "selftest: null argument");
+    unsigned long long* err = nullptr;
+    ORCHA_CUDA(cudaMalloc(&err, 6 * sizeof(unsigned long long)), "selftest alloc");
+    cudaError_t e = cudaMemset(err, 0, 6 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = orcha::launch_selftest_dword(count, seed, err, nullptr);
+    unsigned long long h[6] = {};
+    if (e == cudaSuccess) e = cudaMemcpy(h, err, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    for (int k = 0; k < 6; ++k) std::memcpy(&max_err[k], &h[k], sizeof(double));
     return ORCHA_OK;
 }
 

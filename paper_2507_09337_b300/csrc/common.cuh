@@ -269,6 +269,45 @@ template <> struct P<float> {
     static __device__ __forceinline__ double to_double(float x) { return to_f64(x); }
 };
 
+// ---------------------------------------------------------------- double-word (FF task)
+// Reconstruction, predictor and HLL fluxes in double-word arithmetic
+// (dword.cuh, ~48 bits on the FP32 pipe); the conserved-state update, the
+// guard fill and the dt reduction stay FP64.
+}  // namespace orcha
+#include "dword.cuh"
+namespace orcha {
+template <> __device__ __forceinline__ dw as<dw, dw>(dw x) { return x; }
+template <> struct P<dw> {
+    using store = dw;
+    // binary64 -> double-word: hi = x rounded to binary32, lo = (x - hi)
+    // rounded (x - hi is exact in binary64); |x - (hi + lo)| <= 2^-49 |x|
+    static __device__ __forceinline__ dw in(double x) {
+        const float h = __double2float_rn(x);
+        return {h, __double2float_rn(__dsub_rn(x, to_f64(h)))};
+    }
+    static __device__ __forceinline__ dw rcp(dw x) { return dw_rcp(x); }
+    static __device__ __forceinline__ dw sqrt(dw x) { return x.hi > 0.0f ? x * dw_rsqrt(x) : dw{0.0f, 0.0f}; }
+    static __device__ __forceinline__ dw sound(dw x, dw rho) {
+        return x.hi > 0.0f ? x * dw_rsqrt(x * rho) : dw{0.0f, 0.0f};
+    }
+    static __device__ __forceinline__ dw ld(const dw* p) { return *p; }
+    static __device__ __forceinline__ void st(dw* p, dw x) { *p = x; }
+    // signs and order of a normalised double-word are those of its high part
+    static __device__ __forceinline__ bool pos(dw x) { return x.hi > 0.0f; }
+    static __device__ __forceinline__ bool neg(dw x) { return x.hi < 0.0f; }
+    static __device__ __forceinline__ bool lt(dw a, dw b) { return dw_lt(a, b); }
+    static __device__ __forceinline__ bool ge0(dw a) { return a.hi >= 0.0f; }
+    static __device__ __forceinline__ bool le0(dw a) { return a.hi <= 0.0f; }
+    static __device__ __forceinline__ dw minmod(dw a, dw b) {
+        if (a.hi > 0.0f && b.hi > 0.0f) return dw_lt(a, b) ? a : b;
+        if (a.hi < 0.0f && b.hi < 0.0f) return dw_lt(b, a) ? a : b;
+        return dw{0.0f, 0.0f};
+    }
+    static __device__ __forceinline__ dw half(dw x) { return {__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)}; }
+    static __device__ __forceinline__ dw zero() { return dw{0.0f, 0.0f}; }
+    static __device__ __forceinline__ double to_double(dw x) { return __dadd_rn(to_f64(x.hi), to_f64(x.lo)); }
+};
+
 // ---------------------------------------------------------------- float-float (error-free transformations)
 // A value carried as an unevaluated sum hi + lo of two floats (about 46
 // significant bits). two_sum (Knuth) and two_prod (with FMA) are exact.

@@ -441,10 +441,14 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     // x, y, z terms are summed as float-float (about 46 bits); only the final
     // U+ = U - (sum) is FP64 arithmetic. The same face value enters both cells,
     // so the sum still telescopes to ~1e-14 of each term.
+    // FF path: the differences and their c_d scaling and sum are double-word,
+    // the final U+ = U - (sum) FP64.
     constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr bool DW = std::is_same<T, dw>::value;
     T zp_prev[NV], Fz_prev[NV];
     double acc_prev[NV];
     ff acc_ff[NV];
+    dw acc_dw[NV];
     unsigned long long smaxb = 0ull;   // bits of the largest signal speed
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -452,7 +456,11 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         Fz_prev[v] = P<T>::zero();
         acc_prev[v] = 0.0;
         acc_ff[v] = {0.0f, 0.0f};
+        acc_dw[v] = {0.0f, 0.0f};
     }
+    dw cdw[3];                           // c_d as double-words (FF path)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) cdw[d] = DW ? P<dw>::in(cd[d]) : dw{0.0f, 0.0f};
     float ch[3], cl[3];                  // c_d = dt/dx_d as float pairs (FP32-flux path)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -558,6 +566,9 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                     if constexpr (F32) {
                         const ff tz = ff_scale(ff_diff(Fz[v], Fz_prev[v]), ch[2], cl[2]);
                         Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
+                    } else if constexpr (DW) {
+                        const dw tz = cdw[2] * (Fz[v] - Fz_prev[v]);
+                        Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
                     } else {
                         const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
                         const rd acc = rd(acc_prev[v]) + tz;
@@ -579,6 +590,10 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                     const ff tx = ff_scale(ff_diff(sFx[v * Tl::NXF + fx + 1], sFx[v * Tl::NXF + fx]), ch[0], cl[0]);
                     const ff ty = ff_scale(ff_diff(sFy[v * Tl::NYF + fy + TX], sFy[v * Tl::NYF + fy]), ch[1], cl[1]);
                     acc_ff[v] = ff_add(tx, ty);
+                } else if constexpr (DW) {
+                    const dw tx = cdw[0] * (P<T>::ld(&sFx[v * Tl::NXF + fx + 1]) - P<T>::ld(&sFx[v * Tl::NXF + fx]));
+                    const dw ty = cdw[1] * (P<T>::ld(&sFy[v * Tl::NYF + fy + TX]) - P<T>::ld(&sFy[v * Tl::NYF + fy]));
+                    acc_dw[v] = tx + ty;
                 } else {
                     const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx + 1]))) -
                                                rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx]))));
@@ -593,6 +608,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if constexpr (F32) Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(acc_ff[v]));
+                    else if constexpr (DW) Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v]));
                     else Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }

@@ -312,6 +312,56 @@ __global__ void selftest_fp64_kernel(unsigned long long n, unsigned long long se
     if (cnt) atomicAdd(bad, cnt);
 }
 
+// Double-word arithmetic (dword.cuh) against FP64 references on pseudo-random
+// operands (magnitudes 2^-30 .. 2^30, both signs; half of the sum operand
+// pairs nearly cancel). Every double-word here is exactly a binary64 value
+// (hi + lo spans at most 49 bits), so the references A op B are FP64
+// operations on the exact operands, themselves within 2^-53 of the true
+// result. Raises err[k] to the largest error of: 0 binary64 -> double-word,
+// 1 sum (relative to |A| + |B|), 2 product, 3 reciprocal, 4 reciprocal
+// square root, 5 sound speed sqrt(X / R) as X rsqrt(X R) (relative).
+__device__ __forceinline__ double st_double(unsigned long long r) {
+    const unsigned long long e = 1023 - 30 + (r >> 52) % 61;
+    return __longlong_as_double((long long)(((r >> 63) << 63) | (e << 52) | (r & kM52)));
+}
+__device__ __forceinline__ void st_raise(unsigned long long* slot, double v) {
+    atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+__global__ void selftest_dword_kernel(unsigned long long n, unsigned long long seed, unsigned long long* err) {
+    double mx[6] = {0, 0, 0, 0, 0, 0};
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r1 = mix64(seed + 2 * i), r2 = mix64(seed + 2 * i + 1);
+        const double x = st_double(r1);
+        double y = st_double(r2);
+        if (r2 & 1) {   // nearly cancelling partner: -x with its low mantissa bits perturbed
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x) ^ (1ull << 63);
+            y = __longlong_as_double((long long)(b ^ ((r2 >> 8) & ((1ull << (1 + (r2 >> 58) % 40)) - 1ull))));
+        }
+        const dw a = P<dw>::in(x), b = P<dw>::in(y);
+        const double A = P<dw>::to_double(a), B = P<dw>::to_double(b);
+        mx[0] = fmax(mx[0], fabs(__dsub_rn(A, x)) / fabs(x));
+        mx[1] = fmax(mx[1], fabs(__dsub_rn(P<dw>::to_double(a + b), __dadd_rn(A, B))) / (fabs(A) + fabs(B)));
+        const double AB = __dmul_rn(A, B);
+        mx[2] = fmax(mx[2], fabs(__dsub_rn(P<dw>::to_double(a * b), AB)) / fabs(AB));
+        const double iA = __drcp_rn(A);
+        mx[3] = fmax(mx[3], fabs(__dsub_rn(P<dw>::to_double(dw_rcp(a)), iA)) / fabs(iA));
+        const dw aa = {fabsf(a.hi), a.hi < 0.0f ? -a.lo : a.lo}, bb = {fabsf(b.hi), b.hi < 0.0f ? -b.lo : b.lo};
+        const double rs = __drcp_rn(__dsqrt_rn(fabs(A)));
+        mx[4] = fmax(mx[4], fabs(__dsub_rn(P<dw>::to_double(dw_rsqrt(aa)), rs)) / rs);
+        const double c = __dsqrt_rn(__ddiv_rn(fabs(A), fabs(B)));
+        mx[5] = fmax(mx[5], fabs(__dsub_rn(P<dw>::to_double(P<dw>::sound(aa, bb)), c)) / c);
+    }
+    for (int k = 0; k < 6; ++k) st_raise(err + k, mx[k]);
+}
+
+cudaError_t launch_selftest_dword(unsigned long long n, unsigned long long seed, unsigned long long* err,
+                                  cudaStream_t st) {
+    selftest_dword_kernel<<<148 * 8, 256, 0, st>>>(n, seed, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_selftest_fp64(unsigned long long n, unsigned long long seed, unsigned long long* bad,
                                  cudaStream_t st) {
     selftest_fp64_kernel<<<148 * 16, 256, 0, st>>>(n, seed, bad);
@@ -365,10 +415,11 @@ static cudaError_t occupancy_t(int* per_sm) {
 
 #define ORCHA_PERS_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y)                                                              \
-        return f32 ? launch_persistent_t<ND, X, Y, float>(slots, items, nitems, queue, grid, st)       \
-                   : launch_persistent_t<ND, X, Y, rd>(slots, items, nitems, queue, grid, st);
+        return prec == kF32  ? launch_persistent_t<ND, X, Y, float>(slots, items, nitems, queue, grid, st) \
+               : prec == kFF ? launch_persistent_t<ND, X, Y, dw>(slots, items, nitems, queue, grid, st)    \
+                             : launch_persistent_t<ND, X, Y, rd>(slots, items, nitems, queue, grid, st);
 
-cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev* slots, const Item* items,
+cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
                               int nitems, unsigned* queue, int grid, cudaStream_t st) {
     ORCHA_PERS_CASE(2, 8, 8)
     ORCHA_PERS_CASE(2, 16, 8)
@@ -380,9 +431,12 @@ cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev*
 }
 
 #define ORCHA_OCC_CASE(ND, X, Y)                                                                       \
-    if (ndim == ND && tx == X && ty == Y) return f32 ? occupancy_t<ND, X, Y, float>(per_sm) : occupancy_t<ND, X, Y, rd>(per_sm);
+    if (ndim == ND && tx == X && ty == Y)                                                              \
+        return prec == kF32  ? occupancy_t<ND, X, Y, float>(per_sm)                                    \
+               : prec == kFF ? occupancy_t<ND, X, Y, dw>(per_sm)                                       \
+                             : occupancy_t<ND, X, Y, rd>(per_sm);
 
-cudaError_t persistent_occupancy(int ndim, int tx, int ty, bool f32, int* per_sm) {
+cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm) {
     ORCHA_OCC_CASE(2, 8, 8)
     ORCHA_OCC_CASE(2, 16, 8)
     ORCHA_OCC_CASE(2, 16, 16)
@@ -394,10 +448,11 @@ cudaError_t persistent_occupancy(int ndim, int tx, int ty, bool f32, int* per_sm
 
 #define ORCHA_TILE_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y)                                                              \
-        return f32 ? launch_hydro_t<ND, X, Y, float>(m, ids, n, Uin, Uout, st)                         \
-                   : launch_hydro_t<ND, X, Y, rd>(m, ids, n, Uin, Uout, st);
+        return prec == kF32  ? launch_hydro_t<ND, X, Y, float>(m, ids, n, Uin, Uout, st)               \
+               : prec == kFF ? launch_hydro_t<ND, X, Y, dw>(m, ids, n, Uin, Uout, st)                  \
+                             : launch_hydro_t<ND, X, Y, rd>(m, ids, n, Uin, Uout, st);
 
-cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* ids, int n, const double* Uin,
+cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
                          double* Uout, cudaStream_t st) {
     const int ndim = m.ndim;
     ORCHA_TILE_CASE(2, 8, 8)
@@ -412,6 +467,7 @@ cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* 
 #define ORCHA_CONF_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y) {                                                            \
         cudaError_t e = configure_t<ND, X, Y, float>();                                                \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, dw>();                                         \
         return e != cudaSuccess ? e : configure_t<ND, X, Y, rd>();                                     \
     }
 

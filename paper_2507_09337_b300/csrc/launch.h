@@ -9,6 +9,15 @@
 
 namespace orcha {
 
+// Arithmetic variants of the hydro kernels: FP64, FP32 reconstruction/flux,
+// double-word reconstruction/flux (all with the FP64 update).
+enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2 };
+constexpr int kNumPrec = 3;
+// Variant of a hydro task, or -1 for any other task.
+inline int prec_of(orcha_task t) {
+    return t == ORCHA_TASK_HYDRO_FP64 ? kF64 : t == ORCHA_TASK_HYDRO_F32FLUX ? kF32 : t == ORCHA_TASK_HYDRO_FF ? kFF : -1;
+}
+
 // Error reporting of the C ABI (sets the calling thread's orcha_last_error).
 orcha_status set_error(orcha_status code, const char* msg);
 orcha_status cuda_error(cudaError_t e, const char* what);
@@ -16,10 +25,10 @@ orcha_status cuda_error(cudaError_t e, const char* what);
 // left null). Host-only.
 orcha_status mesh_dev_from_desc(const orcha_mesh_desc* d, MeshDev* out, long long* nblk_out);
 
-cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, bool f32, const int* ids, int n, const double* Uin,
+cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
                          double* Uout, cudaStream_t st);
 bool hydro_tile_supported(int ndim, int tx, int ty);
-// Set the dynamic shared-memory limit of both precisions of a tile variant on
+// Set the dynamic shared-memory limit of every precision of a tile variant on
 // the current device (call once per device before launching or capturing).
 cudaError_t configure_hydro(int ndim, int tx, int ty);
 cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U, cudaStream_t st);
@@ -45,12 +54,16 @@ cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigne
 // Self-test of the integer-pipe binary64 add/sub/mul (counts mismatches into *bad).
 cudaError_t launch_selftest_fp64(unsigned long long n, unsigned long long seed, unsigned long long* bad,
                                  cudaStream_t st);
+// Self-test of the double-word arithmetic: raises err[0..5] (bits of
+// non-negative doubles) to the largest errors against FP64 references.
+cudaError_t launch_selftest_dword(unsigned long long n, unsigned long long seed, unsigned long long* err,
+                                  cudaStream_t st);
 // Built column-tile variants, widest first.
 constexpr int kTiles[3][2] = {{16, 16}, {16, 8}, {8, 8}};
 // One persistent launch (one time step of every mesh in `slots`).
-cudaError_t launch_persistent(int ndim, int tx, int ty, bool f32, const SlotDev* slots, const Item* items,
+cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
                               int nitems, unsigned* queue, int grid, cudaStream_t st);
 // Resident CTAs per SM of a persistent variant.
-cudaError_t persistent_occupancy(int ndim, int tx, int ty, bool f32, int* per_sm);
+cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm);
 
 }  // namespace orcha

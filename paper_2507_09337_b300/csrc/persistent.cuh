@@ -64,9 +64,12 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // Resident CTAs per SM requested from the register allocator (A/B-measured
 // on a B300): the FP64 variant, bound by the FP64 pipe, gains from 384
 // threads per SM (a small spill; +2 %); the FP32-flux variant runs best at
-// 512 threads per SM (128 registers) and loses from the spills of more.
+// 512 threads per SM (128 registers) and loses from the spills of more. The
+// double-word variant has the FP64 variant's register and shared-memory
+// footprint (8-byte values) and takes its bound.
 template <class T, int NT> struct MinBlocks { static constexpr int value = (512 / NT) > 1 ? (512 / NT) : 1; };
 template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
+template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 
 template <int NDIM, int TX, int TY, class T>
 __global__ void __launch_bounds__(TX * TY, (MinBlocks<T, TX * TY>::value))

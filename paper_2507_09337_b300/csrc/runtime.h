@@ -46,14 +46,14 @@ struct orcha_batch {
     std::vector<const orcha_packet*> packets;
     int ndim = 3, tx = 8, ty = 8;
     std::vector<orcha::Item> base_items;             // full-block items in packet order
-    // per precision (0: FP64, 1: FP32 flux): work list sized for that variant's occupancy
+    // per precision (orcha::Prec): work list sized for that variant's occupancy
     struct List {
         bool built = false;
         int nitems = 0, grid = 0;
         orcha::Item* items_dev = nullptr;
         orcha::SlotDev* slots_dev = nullptr;
         unsigned* done_dev = nullptr;
-    } lists[2];
+    } lists[3];
     unsigned* queue = nullptr;
     int* cur_dev = nullptr;
     int num_sms = 0;

@@ -107,20 +107,21 @@ struct Req {
     double* partial = nullptr;       // nblk x 5 doubles: per-block sums of the totals reduction
     int cur_host = 0, steps_left = 0, nitems = 0, err_slot = -1;
     int tx = 8, ty = 8;              // column tile of the hydro launch this request joins
-    bool f32 = false;
+    int prec = orcha::kF64;          // arithmetic variant of the hydro task (orcha::Prec)
     cudaEvent_t ev = nullptr;        // admission done / completion landed
     RS st = RS::Pending;
     orcha_request_stats stats{};
 };
 
-// One launch per (ndim 2 or 3) x (FP64 or FP32 flux) x (tile 8x8 or 16x8):
-// blocks of 16 or more cells across x use the 16x8 tile (the autotuner's
-// choice for 16^3 blocks on a B300), 8-cell blocks the 8x8 one.
-constexpr int kGroups = 8;
-__host__ __device__ constexpr int group_ndim(int g) { return 2 + ((g >> 1) & 1); }
-__host__ __device__ constexpr int group_f32(int g) { return g & 1; }
-__host__ __device__ constexpr int group_tx(int g) { return (g >> 2) ? 16 : 8; }
-constexpr int group_of(int ndim, bool f32, int tx) { return (tx == 16 ? 4 : 0) | ((ndim - 2) << 1) | (f32 ? 1 : 0); }
+// One launch per (ndim 2 or 3) x (FP64, FP32 flux or FF) x (tile 8x8 or
+// 16x8): blocks of 16 or more cells across x use the 16x8 tile (the
+// autotuner's choice for 16^3 blocks on a B300), 8-cell blocks the 8x8 one.
+constexpr int kGroups = 2 * orcha::kNumPrec * 2;
+__host__ __device__ constexpr int group_ndim(int g) { return 2 + (g & 1); }
+__host__ __device__ constexpr int group_prec(int g) { return (g >> 1) % orcha::kNumPrec; }
+__host__ __device__ constexpr int group_tx(int g) { return (g >> 1) / orcha::kNumPrec ? 16 : 8; }
+constexpr int group_of(int ndim, int prec, int tx) { return (ndim - 2) | ((prec + (tx == 16 ? orcha::kNumPrec : 0)) << 1); }
+static_assert(group_of(group_ndim(11), group_prec(11), group_tx(11)) == 11, "group index round trip");
 
 struct GroupBuf {                    // host/device work list of one launch
     std::vector<orcha::SlotDev> slots_h;
@@ -170,7 +171,7 @@ struct orcha_server {
     bool fail(orcha_status s, const std::string& msg);
     bool admit(Req* r);
     bool launch_step(bool* launched);
-    int occ[kGroups] = {0, 0, 0, 0};             // resident CTAs per SM of each group's variant
+    int occ[kGroups] = {};                       // resident CTAs per SM of each group's variant
     bool complete(Req* r);
 };
 
@@ -250,13 +251,13 @@ bool orcha_server::launch_step(bool* launched) {
     }
     std::vector<Req*> finished;
     for (int gi = 0; gi < kGroups; ++gi) {
-        const int ndim = group_ndim(gi), f32 = group_f32(gi), gtx = group_tx(gi), gty = 8;
+        const int ndim = group_ndim(gi), prec = group_prec(gi), gtx = group_tx(gi), gty = 8;
         GroupBuf& g = s.g[gi];
         g.slots_h.clear();
         g.items_h.clear();
         std::vector<Req*> grp;
         for (Req* r : active)
-            if (group_of(r->m.ndim, r->f32, r->tx) == gi) grp.push_back(r);
+            if (group_of(r->m.ndim, r->prec, r->tx) == gi) grp.push_back(r);
         if (grp.empty()) continue;
         for (size_t i = 0; i < grp.size(); ++i) {
             Req* r = grp[i];
@@ -298,7 +299,7 @@ bool orcha_server::launch_step(bool* launched) {
                                  cudaMemcpyHostToDevice, compute), "step upload");
         SRV_CUDA(cudaMemsetAsync(g.queue_d, 0, sizeof(unsigned), compute), "step queue");
         const int grid = std::max(1, std::min((int)g.items_h.size(), occ[gi] * num_sms));
-        SRV_CUDA(orcha::launch_persistent(ndim, gtx, gty, f32, g.slots_d, g.items_d, (int)g.items_h.size(),
+        SRV_CUDA(orcha::launch_persistent(ndim, gtx, gty, prec, g.slots_d, g.items_d, (int)g.items_h.size(),
                                           g.queue_d, grid, compute), "step launch");
         for (Req* r : grp) {
             r->cur_host ^= 1;
@@ -434,7 +435,7 @@ orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, or
         if (e == cudaSuccess) e = orcha::configure_hydro(nd, 16, 8);
     }
     for (int gi = 0; e == cudaSuccess && gi < kGroups; ++gi)
-        e = orcha::persistent_occupancy(group_ndim(gi), group_tx(gi), 8, group_f32(gi), &s->occ[gi]);
+        e = orcha::persistent_occupancy(group_ndim(gi), group_tx(gi), 8, group_prec(gi), &s->occ[gi]);
     if (e != cudaSuccess) {
         orcha_status st = orcha::cuda_error(e, "server_create");
         s->stop = true;
@@ -485,7 +486,7 @@ orcha_status orcha_server_destroy(orcha_server* s) {
 orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, int64_t* ticket) {
     if (!s || !rd || !ticket) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: null argument");
     if (rd->nsteps < 1) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: nsteps < 1");
-    if (rd->task != ORCHA_TASK_HYDRO_FP64 && rd->task != ORCHA_TASK_HYDRO_F32FLUX)
+    if (orcha::prec_of((orcha_task)rd->task) < 0)
         return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: task must be a hydro task");
     if (rd->init_kind == ORCHA_INIT_FROM_HOST && !rd->init_host)
         return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: FROM_HOST needs init_host");
@@ -508,7 +509,7 @@ orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, 
     orcha_status st = orcha::mesh_dev_from_desc(&md, &r->m, &r->nblk);
     if (st) { delete r; return st; }
     r->d = *rd;
-    r->f32 = rd->task == ORCHA_TASK_HYDRO_F32FLUX;
+    r->prec = orcha::prec_of((orcha_task)rd->task);
     r->ncell = (long long)rd->bs[0] * rd->bs[1] * (rd->ndim == 3 ? rd->bs[2] : 1);
     r->interior_bytes = (size_t)r->nblk * r->m.nvar * r->ncell * sizeof(double);
     r->state_elems = orcha_state_elems(&md);

@@ -76,22 +76,23 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_mixed_precision_and_block_sizes_in_flight_together():
-    reqs = _requests(6, 5, sizes=(8, 16, 32), max_blocks=4, nsteps=2)
-    a64 = [_serve([r])[0][0] for r in reqs[:3]]
-    a32 = [_serve([r], task=B.ORCHA_TASK_HYDRO_F32FLUX)[0][0] for r in reqs[3:]]
+    """FP64, FP32-flux and FF requests of block sizes 8, 16 and 32 in flight
+    together: each result equals the same request served alone."""
+    reqs = _requests(9, 5, sizes=(8, 16, 32), max_blocks=4, nsteps=2)
+    tasks = [B.ORCHA_TASK_HYDRO_FP64] * 3 + [B.ORCHA_TASK_HYDRO_F32FLUX] * 3 + [B.ORCHA_TASK_HYDRO_FF] * 3
+    alone = [_serve([r], task=t)[0][0] for r, t in zip(reqs, tasks)]
     srv = serve.Server(8 << 30)
     try:
         keep, tickets = [], []
-        for i, r in enumerate(reqs):
+        for r, task in zip(reqs, tasks):
             U0, init, out = _host_buffers(r)
             keep.append((init, out))
-            task = B.ORCHA_TASK_HYDRO_FP64 if i < 3 else B.ORCHA_TASK_HYDRO_F32FLUX
             tickets.append(srv.submit(serve.request_desc(r, task, init.data_ptr(), out.data_ptr())))
         for t in tickets:
-            srv.wait(t)
+            assert srv.wait(t).status == 0
     finally:
         srv.close()
-    for (init, out), a in zip(keep, a64 + a32):
+    for (init, out), a in zip(keep, alone):
         assert np.array_equal(out.numpy(), a)
 
 
