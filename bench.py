@@ -238,6 +238,7 @@ def main():
     out_dev = torch.empty_like(U0_dev)
     mesh = B.Mesh(spec, device=f"cuda:{local}", packets=packets)
     stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))   # buffers were set up on the current stream
     npk = len(mesh.packets)
     h = mesh.handle
     # tile shape picked by the autotuner (cached per GPU and geometry; outside the timed region)

@@ -54,13 +54,18 @@ __device__ __forceinline__ dw operator+(dw x, dw y) {
 }
 __device__ __forceinline__ dw operator-(dw x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+// The product is returned as the pair (ch, cl) before the final Fast2Sum:
+// the same value (Fast2Sum is exact) with |cl| <= ~2u |ch| instead of
+// u |ch|. Every consumer accepts that: sums and products use the low part
+// only in rounded terms, the reciprocal and rsqrt fold it into their
+// residual, the conversion to binary64 is still exact, and a sign test reads
+// the high part, whose sign is the value's. Comparisons (dw_lt) are only
+// applied to sums, which are normalised.
 __device__ __forceinline__ dw operator*(dw x, dw y) {
     const float ch = __fmul_rn(x.hi, y.hi);
     const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);            // x.hi * y.hi = ch + cl1 exactly
     const float cl2 = __fmaf_rn(x.lo, y.hi, __fmul_rn(x.hi, y.lo));
-    dw z;
-    dwx::fast_two_sum(ch, __fadd_rn(cl1, cl2), z.hi, z.lo);
-    return z;
+    return {ch, __fadd_rn(cl1, cl2)};
 }
 
 // 1 / y: r1 = the hardware reciprocal of y.hi refined by one FP32 Newton

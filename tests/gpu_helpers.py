@@ -51,6 +51,7 @@ def gpu_steps(spec, U0, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, packets=None, tile
                 B.orcha_mesh_swap(mesh.handle)
         else:
             s = torch.cuda.Stream() if use_graph else stream
+            s.wait_stream(stream)          # the load above was enqueued on the current stream
             with torch.cuda.stream(s):
                 mesh.advance(nsteps, task, init_dt=True, use_graph=use_graph, stream=s)
             s.synchronize()
