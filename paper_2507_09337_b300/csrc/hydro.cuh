@@ -381,11 +381,14 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 
     // P: slopes, predictor and face states of the cell at R2 index c2 of plane
     // pzi; writes flo/fhi (face states on the low/high side along each axis).
-    auto predict = [&](int pzi, int c2, T (&flo)[3][NV], T (&fhi)[3][NV]) {
-        using A = Arith<T, 2>;     // arithmetic type of the predictor
+    // P: slopes and predictor of the cell at R2 index c2 of plane pzi: its
+    // primitives Wc, limited slopes dW and half-step state Wb.
+    using A2 = Arith<T, 2>;      // arithmetic type of the predictor
+    auto predict_core = [&](int pzi, int c2, A2 (&Wc)[NV], A2 (&dW)[3][NV], A2 (&Wb)[NV]) {
+        using A = A2;
         const int sc = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
         const S* w = sW + sc * NW * R2N;
-        A Wc[NV], dW[3][NV], a[3][NV];
+        A a[3][NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) Wc[v] = as<A>(P<T>::ld(&w[v * R2N + c2]));
         const A rc = as<A>(P<T>::ld(&w[NV * R2N + c2]));
@@ -417,7 +420,6 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 a[d][1 + t] = (t == d) ? ((un * dun) + (dp * rc)) : (un * dW[d][1 + t]);
             a[d][NV - 1] = (gp * dun) + (un * dp);
         }
-        A Wb[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             if constexpr (kContract && std::is_same<A, rd>::value) {
@@ -432,12 +434,28 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 Wb[v] = Wc[v] - s;
             }
         }
+    };
+    // First-order fallback test: every face state's density and pressure positive.
+    auto faces_ok = [&](const A2 (&dW)[3][NV], const A2 (&Wb)[NV]) {
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const A2 h0 = P<A2>::half(dW[d][0]), hp = P<A2>::half(dW[d][NV - 1]);
+            ok = ok && P<T>::pos(as<T>(Wb[0] - h0)) && P<T>::pos(as<T>(Wb[NV - 1] - hp)) &&
+                 P<T>::pos(as<T>(Wb[0] + h0)) && P<T>::pos(as<T>(Wb[NV - 1] + hp));
+        }
+        return ok;
+    };
+    // Owner cells: every face state Wb -+ dW/2 (flo / fhi), or Wc on fallback.
+    auto predict = [&](int pzi, int c2, T (&flo)[3][NV], T (&fhi)[3][NV]) {
+        A2 Wc[NV], dW[3][NV], Wb[NV];
+        predict_core(pzi, c2, Wc, dW, Wb);
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const A hs = P<A>::half(dW[d][v]);
+                const A2 hs = P<A2>::half(dW[d][v]);
                 flo[d][v] = as<T>(Wb[v] - hs);
                 fhi[d][v] = as<T>(Wb[v] + hs);
             }
@@ -449,6 +467,21 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             for (int d = 0; d < NDIM; ++d)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) { flo[d][v] = as<T>(Wc[v]); fhi[d][v] = as<T>(Wc[v]); }
+        }
+    };
+    // Ring cells: only the one x or y face state the tile needs (face 0..3 =
+    // x-, x+, y-, y+), the same values the owner of that cell would form.
+    auto predict_face = [&](int pzi, int c2, int face, T (&out)[NV]) {
+        A2 Wc[NV], dW[3][NV], Wb[NV];
+        predict_core(pzi, c2, Wc, dW, Wb);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const A2 hs = P<A2>::half(face < 2 ? dW[0][v] : dW[1][v]);
+            out[v] = as<T>(Wb[v] + ((face & 1) ? hs : -hs));     // Wb + hs or Wb - hs, same bits
+        }
+        if (!faces_ok(dW, Wb)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] = as<T>(Wc[v]);
         }
     };
 
@@ -523,14 +556,10 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             }
         }
         if (inner && tid < Tl::NRING) {
-            T flo[3][NV], fhi[3][NV];
-            predict(p, rc2, flo, fhi);
-            // the one face state this ring cell contributes (selects keep the arrays in registers)
+            T fs[NV];
+            predict_face(p, rc2, rface, fs);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const T val = rface == 0 ? flo[0][v] : rface == 1 ? fhi[0][v] : rface == 2 ? flo[1][v] : fhi[1][v];
-                P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], val);
-            }
+            for (int v = 0; v < NV; ++v) P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs[v]);
         }
         __syncthreads();
 
