@@ -117,16 +117,16 @@ def test_batch_validation():
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (16, 8)])
-def test_tail_wave_split_into_z_halves_keeps_the_bits(tile):
+def test_tail_wave_split_into_z_slabs_keeps_the_bits(tile):
     """512 blocks of 16^3 leave a partial last wave of resident CTAs, whose
-    items the batch splits into two z halves: the result is bitwise the packet
-    path's (every face flux is the same expression whichever item computes it)."""
+    items the batch splits into z slabs (two, or three for the FF variant with
+    16x8 tiles on a B300): the result is bitwise the packet path's (every face
+    flux is the same expression whichever item computes it), in all three
+    arithmetic variants."""
     spec, packets = wl.sedov128_packets(64)
     U0 = wl.random_blocky_state(spec, 71)
-    A, _, _ = gpu_steps(spec, U0, 3, packets=packets)
-    (G,), errs = gpu_batch_steps([(spec, U0, packets)], 3, tile=tile)
-    assert errs == [0]
-    assert np.array_equal(G, A)
-    (F,), _ = gpu_batch_steps([(spec, U0, packets)], 3, tile=tile, task=B.ORCHA_TASK_HYDRO_F32FLUX)
-    P, _, _ = gpu_steps(spec, U0, 3, packets=packets, task=B.ORCHA_TASK_HYDRO_F32FLUX)
-    assert np.array_equal(F, P)
+    for task in (B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_FF):
+        A, _, _ = gpu_steps(spec, U0, 3, packets=packets, task=task)
+        (G,), errs = gpu_batch_steps([(spec, U0, packets)], 3, tile=tile, task=task)
+        assert errs == [0]
+        assert np.array_equal(G, A), task
