@@ -151,6 +151,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- replicas: timing over ranks
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is none): the whole job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all replicas processed over the slowest
+    replica's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------- the oracle on the host cores
 
 def oracle_rate(spec, U0, seconds: float, max_steps: int = 400):
@@ -288,15 +308,11 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dev)
     assert mesh.poll(stream) == 0
 
     zone_updates = spec.zones * nt * args.steps * world
-    value = zone_updates / (ms_max * 1e-3)
+    value = job_rate(spec.zones * nt * args.steps, world, ms_max)
 
     # dominant kernel: the hydro task, timed per launch on its own stream
     durs = [(a.elapsed_time(b) * 1e-3, nblk) for a, b, nblk in hydro_events]
@@ -369,10 +385,7 @@ def main():
     stream.wait_event(mid)
     e1.record(stream)
     stream.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = zone_updates / (float(e2e_ms.item()) * 1e-3)
+    e2e_value = job_rate(spec.zones * nt * args.steps, world, max_over_ranks(e0.elapsed_time(e1), dev))
     assert mesh2.poll(stream2) == 0
     assert mesh.poll(stream) == 0
     # the e2e runs and the device-resident run computed the same state
