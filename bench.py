@@ -308,7 +308,8 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, dev)
     assert mesh.poll(stream) == 0
 
     zone_updates = spec.zones * nt * args.steps * world
