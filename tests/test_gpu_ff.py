@@ -30,15 +30,16 @@ def test_dword_building_blocks_error_bounds():
     """Largest errors of the double-word operations on 2^26 operand pairs,
     in units of u^2, against bounds from their error analysis: the split
     (2^-49 relative = u^2 / 2); the sum, relative to |x| + |y|: u^2 from
-    adding the low parts plus 2 u^2 from adding that to the high parts'
-    rounding error, plus the FP64 reference's own 2^-53; the product 7 u^2
+    adding the low parts, 2 u^2 from adding that to the high parts' rounding
+    error, 2 u^2 from Fast2Sum when cancellation leaves |w| > |sh|, plus the
+    FP64 reference's own 2^-53; the product 7 u^2
     (the dropped lo*lo term u^2, two roundings of the cross terms 3 u^2, the
     final sum 3 u^2); reciprocal, rsqrt and sound speed a few u^2 (roundings
     of the Newton correction, whose size is about u)."""
     e = B.orcha_selftest_dword(1 << 26, seed=99)
     names = ["split", "sum", "product", "reciprocal", "rsqrt", "sound speed"]
     print("double-word max errors in u^2:", {n: round(v / U2, 3) for n, v in zip(names, e)})
-    bounds = [0.5, 3.1, 7.0, 8.0, 10.0, 20.0]
+    bounds = [0.5, 5.1, 7.0, 8.0, 10.0, 20.0]
     for n, v, b in zip(names, e, bounds):
         assert np.isfinite(v) and v <= b * U2, (n, v / U2)
 
