@@ -184,6 +184,22 @@ ORCHA_API orcha_status orcha_packet_destroy(orcha_packet* packet);
  * them. Errors: INVALID, UNSUPPORTED (block size), CUDA (launch). */
 ORCHA_API orcha_status orcha_packet_run(orcha_packet* packet, orcha_task task, void* stream);
 
+/* Unpack a packet (the paper's "moving data back", section "DataItem
+ * Generators"): copy the interiors of the packet's blocks, in packet order
+ * ([position in the packet][var][k][j][i] doubles), from the mesh's current
+ * state buffer to dst: host memory when dst_is_host (pinned for the copy to
+ * be asynchronous; staged through a device buffer the packet owns), else
+ * device memory. The blocks stay resident: a hydro task already wrote them in
+ * place, so dst = NULL is a no-op, and the copy is made only on request.
+ * Stream-ordered. Errors: INVALID (null packet), OOM, CUDA. */
+ORCHA_API orcha_status orcha_packet_unpack(orcha_packet* packet, double* dst, int32_t dst_is_host, void* stream);
+
+/* Pack a packet: write the interiors of its blocks from src (same layout and
+ * host/device meaning as orcha_packet_unpack) into the mesh's current state
+ * buffer; the other blocks are untouched. Errors: INVALID (null argument),
+ * OOM, CUDA. */
+ORCHA_API orcha_status orcha_packet_pack(orcha_packet* packet, const double* src, int32_t src_is_host, void* stream);
+
 /* dt_dev = cfl / (largest signal speed raised since the previous reduce, over
  * all blocks), then clear the signal-speed array. A non-positive or
  * non-finite maximum sets ORCHA_DEVERR_BAD_DT and leaves dt_dev unchanged. */

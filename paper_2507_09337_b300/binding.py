@@ -111,6 +111,8 @@ SIGNATURES = {
     "orcha_packet_create": (_st, [_vp, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp)]),
     "orcha_packet_destroy": (_st, [_vp]),
     "orcha_packet_run": (_st, [_vp, ctypes.c_int, _vp]),
+    "orcha_packet_unpack": (_st, [_vp, _vp, _i32, _vp]),
+    "orcha_packet_pack": (_st, [_vp, _vp, _i32, _vp]),
     "orcha_dt_reduce": (_st, [_vp, _vp]),
     "orcha_mesh_advance": (_st, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _i32, _i32, _i32, _vp]),
     "orcha_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _i32, _i32, ctypes.POINTER(_vp)]),
@@ -223,6 +225,14 @@ def orcha_packet_destroy(packet: int) -> None:
 
 def orcha_packet_run(packet: int, task: int, stream=None) -> None:
     _check(lib().orcha_packet_run(packet, int(task), _stream_ptr(stream)))
+
+
+def orcha_packet_unpack(packet: int, dst_ptr: int | None, dst_is_host: bool, stream=None) -> None:
+    _check(lib().orcha_packet_unpack(packet, dst_ptr, int(bool(dst_is_host)), _stream_ptr(stream)))
+
+
+def orcha_packet_pack(packet: int, src_ptr: int, src_is_host: bool, stream=None) -> None:
+    _check(lib().orcha_packet_pack(packet, src_ptr, int(bool(src_is_host)), _stream_ptr(stream)))
 
 
 def orcha_dt_reduce(mesh: int, stream=None) -> None:

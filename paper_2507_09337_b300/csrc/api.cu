@@ -274,7 +274,49 @@ orcha_status orcha_packet_destroy(orcha_packet* p) {
     if (!p) return ORCHA_OK;
     cudaDeviceSynchronize();
     cudaFree(p->ids_dev);
+    cudaFree(p->staging);
     delete p;
+    return ORCHA_OK;
+}
+
+static orcha_status ensure_packet_staging(orcha_packet* p) {
+    if (p->staging) return ORCHA_OK;
+    const size_t n = (size_t)p->n * p->mesh->dev.nvar * p->mesh->ncell;
+    ORCHA_CUDA(cudaMalloc(&p->staging, n * sizeof(double)), "packet staging buffer");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_packet_unpack(orcha_packet* p, double* dst, int32_t dst_is_host, void* stream) {
+    if (!p) return fail(ORCHA_ERR_INVALID, "packet_unpack: null packet");
+    if (!dst) return ORCHA_OK;                       // blocks are resident and were updated in place
+    orcha_mesh* m = p->mesh;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* U = m->desc.state_dev[m->cur];
+    if (!dst_is_host) {
+        ORCHA_CUDA(orcha::launch_unpack_ids(m->dev, p->ids_dev, p->n, U, dst, st), "packet_unpack");
+        return ORCHA_OK;
+    }
+    orcha_status s = ensure_packet_staging(p);
+    if (s) return s;
+    ORCHA_CUDA(orcha::launch_unpack_ids(m->dev, p->ids_dev, p->n, U, p->staging, st), "packet_unpack");
+    const size_t bytes = (size_t)p->n * m->dev.nvar * m->ncell * sizeof(double);
+    ORCHA_CUDA(cudaMemcpyAsync(dst, p->staging, bytes, cudaMemcpyDeviceToHost, st), "packet_unpack D2H");
+    return ORCHA_OK;
+}
+
+orcha_status orcha_packet_pack(orcha_packet* p, const double* src, int32_t src_is_host, void* stream) {
+    if (!p || !src) return fail(ORCHA_ERR_INVALID, "packet_pack: null argument");
+    orcha_mesh* m = p->mesh;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* from = src;
+    if (src_is_host) {
+        orcha_status s = ensure_packet_staging(p);
+        if (s) return s;
+        const size_t bytes = (size_t)p->n * m->dev.nvar * m->ncell * sizeof(double);
+        ORCHA_CUDA(cudaMemcpyAsync(p->staging, src, bytes, cudaMemcpyHostToDevice, st), "packet_pack H2D");
+        from = p->staging;
+    }
+    ORCHA_CUDA(orcha::launch_pack_ids(m->dev, p->ids_dev, p->n, from, m->desc.state_dev[m->cur], st), "packet_pack");
     return ORCHA_OK;
 }
 

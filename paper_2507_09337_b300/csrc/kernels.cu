@@ -76,6 +76,31 @@ __global__ void unpack_kernel(const MeshDev m, const double* __restrict__ U, dou
         interior[e] = U[padded_offset(m, e, ncell)];
 }
 
+// The same for the blocks of one packet: `interior` holds them in packet
+// order, [packet position][var][k][j][i].
+__device__ __forceinline__ long long packet_offset(const MeshDev& m, const int* ids, long long e, long long ncell) {
+    const long long per_blk = (long long)m.nvar * ncell;
+    return padded_offset(m, (long long)ids[e / per_blk] * per_blk + e % per_blk, ncell);
+}
+
+__global__ void pack_ids_kernel(const MeshDev m, const int* __restrict__ ids, int n,
+                                const double* __restrict__ interior, double* __restrict__ U) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)n * m.nvar * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        U[packet_offset(m, ids, e, ncell)] = interior[e];
+}
+
+__global__ void unpack_ids_kernel(const MeshDev m, const int* __restrict__ ids, int n, const double* __restrict__ U,
+                                  double* __restrict__ interior) {
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const long long total = (long long)n * m.nvar * ncell;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        interior[e] = U[packet_offset(m, ids, e, ncell)];
+}
+
 // ---------------------------------------------------------------- signal speed of the current state
 __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk_ids, const double* __restrict__ U) {
     __shared__ unsigned long long red[32];
@@ -510,6 +535,25 @@ cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cud
 
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st) {
     unpack_kernel<<<copy_grid(m, 256), 256, 0, st>>>(m, U, interior);
+    return cudaGetLastError();
+}
+
+static unsigned packet_grid(const MeshDev& m, int n, int threads) {
+    const long long total = (long long)n * m.nvar * m.bs[0] * m.bs[1] * m.bs[2];
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+cudaError_t launch_pack_ids(const MeshDev& m, const int* ids, int n, const double* interior, double* U,
+                            cudaStream_t st) {
+    pack_ids_kernel<<<packet_grid(m, n, 256), 256, 0, st>>>(m, ids, n, interior, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_ids(const MeshDev& m, const int* ids, int n, const double* U, double* interior,
+                              cudaStream_t st) {
+    unpack_ids_kernel<<<packet_grid(m, n, 256), 256, 0, st>>>(m, ids, n, U, interior);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,11 @@ cudaError_t configure_hydro(int ndim, int tx, int ty);
 cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U, cudaStream_t st);
 cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cudaStream_t st);
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st);
+// Interiors of the blocks ids[0..n) in packet order <-> the padded state.
+cudaError_t launch_pack_ids(const MeshDev& m, const int* ids, int n, const double* interior, double* U,
+                            cudaStream_t st);
+cudaError_t launch_unpack_ids(const MeshDev& m, const int* ids, int n, const double* U, double* interior,
+                              cudaStream_t st);
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
 // Signal speed of every block 0..nblk-1 (one CTA per block, no id list).

@@ -39,6 +39,7 @@ struct orcha_packet {
     int n;
     int* ids_dev;
     std::vector<int> ids;
+    double* staging = nullptr;       // device staging of the packet's interiors for host pack/unpack
 };
 
 struct orcha_batch {
