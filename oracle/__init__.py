@@ -8,8 +8,8 @@ scheme's arithmetic.
 
 Contents:
   * ``oracle.c`` -- the scheme as plain per-block loops (see its header);
-    wrapped here by :func:`step`, :func:`dt`, :func:`run`, :func:`hll`,
-    :func:`minmod`. Pinned by tests/test_oracle_pins.py (exact Sod solution,
+    wrapped here by :func:`step`, :func:`step_rk2`, :func:`stage`, :func:`dt`,
+    :func:`run`, :func:`hll`, :func:`minmod`. Pinned by tests/test_oracle_pins.py (exact Sod solution,
     Sedov radius, conservation, symmetries, free stream, closed-form dt,
     convergence order) and tests/test_oracle_mutations.py (planted mistakes
     are caught).
@@ -56,6 +56,12 @@ def _declare(L):
     L.ora_step.restype = ctypes.c_long
     L.ora_run.argtypes = [mp, dp, ctypes.c_int, dp, dp]
     L.ora_run.restype = ctypes.c_int
+    L.ora_stage.argtypes = [mp, dp, dp, ctypes.c_double, dp, dp]
+    L.ora_stage.restype = ctypes.c_long
+    L.ora_step_rk2.argtypes = [mp, dp, ctypes.c_double, dp, dp]
+    L.ora_step_rk2.restype = ctypes.c_long
+    L.ora_run_scheme.argtypes = [mp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
+    L.ora_run_scheme.restype = ctypes.c_int
     L.ora_set_threads.argtypes = [ctypes.c_int]
     L.ora_set_threads.restype = None
     L.ora_get_threads.argtypes = []
@@ -190,8 +196,36 @@ class Variant:
             raise FloatingPointError("non-physical interior state (rho <= 0 or p <= 0)")
         return Unew, bf, int(nf)
 
-    def run(self, mesh: Mesh, U: np.ndarray, nsteps: int):
-        """nsteps steps, each with dt from the current state.
+    def stage(self, mesh: Mesh, U: np.ndarray, dt_: float, Ubase: np.ndarray | None = None):
+        """One Runge-Kutta stage with the plain MUSCL operator L (no half
+        step): U + dt L(U), or with Ubase the second Heun stage
+        0.5 * (Ubase + (U + dt L(U))). Returns (Unew, bflux, nfirst)."""
+        U = _check_state(mesh, U)
+        base = None if Ubase is None else _check_state(mesh, Ubase)
+        Unew = np.empty_like(U)
+        bf = np.zeros(mesh.nvar)
+        m = mesh.c_struct()
+        nf = self.L.ora_stage(ctypes.byref(m), _ptr(U), None if base is None else _ptr(base), float(dt_),
+                              _ptr(Unew), _ptr(bf))
+        if nf < 0:
+            raise FloatingPointError("non-physical interior state (rho <= 0 or p <= 0)")
+        return Unew, bf, int(nf)
+
+    def step_rk2(self, mesh: Mesh, U: np.ndarray, dt_: float):
+        """One Heun RK2 step (two stages of the plain MUSCL operator).
+        Returns (Unew, bflux, nfirst) with sum Unew = sum U - bflux."""
+        U = _check_state(mesh, U)
+        Unew = np.empty_like(U)
+        bf = np.zeros(mesh.nvar)
+        m = mesh.c_struct()
+        nf = self.L.ora_step_rk2(ctypes.byref(m), _ptr(U), float(dt_), _ptr(Unew), _ptr(bf))
+        if nf < 0:
+            raise FloatingPointError("non-physical interior state (rho <= 0 or p <= 0)")
+        return Unew, bf, int(nf)
+
+    def run(self, mesh: Mesh, U: np.ndarray, nsteps: int, rk2: bool = False):
+        """nsteps steps (MUSCL-Hancock, or Heun RK2 when rk2), each with dt
+        from the current state.
 
         Returns (U_final, dts, bflux_total). The input is not modified.
         """
@@ -199,7 +233,7 @@ class Variant:
         dts = np.zeros(max(nsteps, 1))
         bf = np.zeros(mesh.nvar)
         m = mesh.c_struct()
-        rc = self.L.ora_run(ctypes.byref(m), _ptr(U), int(nsteps), _ptr(dts), _ptr(bf))
+        rc = self.L.ora_run_scheme(ctypes.byref(m), _ptr(U), int(nsteps), int(bool(rk2)), _ptr(dts), _ptr(bf))
         if rc != 0:
             raise FloatingPointError("non-physical state during run")
         return U, dts[:nsteps], bf
@@ -213,4 +247,6 @@ hll = _default.hll
 max_signal_speed = _default.max_signal_speed
 dt = _default.dt
 step = _default.step
+stage = _default.stage
+step_rk2 = _default.step_rk2
 run = _default.run

@@ -17,6 +17,9 @@
  *   guard fill -> primitives -> minmod slopes -> Hancock half-step predictor
  *   -> face states -> HLL (Davis wave speeds) fluxes -> unsplit conservative
  *   update, with dt = CFL / max_cells sum_d (|u_d| + c) / dx_d.
+ * A second integrator, for the paper's Spark solver ("explicit finite
+ * volume, 2nd-order Runge-Kutta", section "Experiments"): Heun's two-stage
+ * method with the same steps minus the half-step predictor (ora_step_rk2).
  * Each step is a function below, in that order, with plain loops over blocks
  * and cells; unstated details are fixed by the "Reading:" notes in place.
  *
@@ -248,9 +251,14 @@ static void fill_padded_block(const ora_mesh* m, const double* U, int bxyz[3], o
 /* Advance one block by dt: reads the global state U (for guards), writes the
  * block's interior into Unew, accumulates domain-boundary fluxes into bflux
  * (units of the cell sum: sum_faces c_d * F, + on the high side, - on the low
- * side), counts first-order cells and non-physical primitives. */
-static void advance_block(const ora_mesh* m, const double* U, double dt, long b, double* Unew,
-                          double* bflux, long* nfirst, long* nbad, ora_work* w) {
+ * side), counts first-order cells and non-physical primitives.
+ * predictor = 1: MUSCL-Hancock (face states from the half-step state);
+ * predictor = 0: plain MUSCL (face states from the stage's own primitives),
+ * the spatial operator of the Runge-Kutta stages. Ubase = NULL: Unew = U - acc
+ * (a forward-Euler stage, or the Hancock step); else the second Heun stage
+ * Unew = 0.5 * (Ubase + (U - acc)), Ubase read at the cell only. */
+static void advance_block(const ora_mesh* m, const double* U, const double* Ubase, int predictor, double dt,
+                          long b, double* Unew, double* bflux, long* nfirst, long* nbad, ora_work* w) {
     int nv = nvars(m), nd = m->ndim;
     double g = m->gamma;
     int bxyz[3] = {(int)(b % m->nb[0]), (int)((b / m->nb[0]) % m->nb[1]), (int)(b / ((long)m->nb[0] * m->nb[1]))};
@@ -313,7 +321,7 @@ static void advance_block(const ora_mesh* m, const double* U, double dt, long b,
                  *      u_t: u_n du_t
                  *      p:   (gamma p) du_n + u_n dp                              */
                 double gp = g * Wc[nv - 1];
-                for (int d = 0; d < nd; ++d) {
+                for (int d = 0; d < nd && predictor; ++d) {
                     double un = Wc[1 + d];
                     double dun = dW[d][1 + d], dp = dW[d][nv - 1];
                     a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);
@@ -322,6 +330,7 @@ static void advance_block(const ora_mesh* m, const double* U, double dt, long b,
                     a[d][nv - 1] = (gp * dun) + (un * dp);
                 }
                 for (int v = 0; v < nv; ++v) {
+                    if (!predictor) { Wbar[v] = Wc[v]; continue; }     /* plain MUSCL: no half step */
                     double s = 0.0;
                     for (int d = 0; d < nd; ++d)
                         s = (d == 0) ? (hd[0] * a[0][v]) : (s + (hd[d] * a[d][v]));
@@ -386,8 +395,11 @@ static void advance_block(const ora_mesh* m, const double* U, double dt, long b,
                     }
                 }
                 long co = ((long)k * m->bs[1] + j) * m->bs[0] + i;
-                for (int v = 0; v < nv; ++v)
-                    Unew[(b * nv + v) * ncell_block(m) + co] = w->U[v * np + c] - acc[v];
+                for (int v = 0; v < nv; ++v) {
+                    long o = (b * nv + v) * ncell_block(m) + co;
+                    double us = w->U[v * np + c] - acc[v];
+                    Unew[o] = Ubase ? (0.5 * (Ubase[o] + us)) : us;
+                }
             }
 }
 
@@ -397,10 +409,12 @@ void ora_set_threads(int n) { n_threads = (n < 1) ? 1 : n; }
 
 int ora_get_threads(void) { return n_threads; }
 
-/* One time step of every block: Unew = step(U, dt). bflux (nvar doubles, may
- * be NULL) receives the boundary-flux total of this step; returns the number
- * of first-order cells, or -1 if an interior cell had rho <= 0 or p <= 0. */
-long ora_step(const ora_mesh* m, const double* U, double dt, double* Unew, double* bflux) {
+/* One pass of advance_block over every block (see there for predictor and
+ * Ubase). bflux (nvar doubles, may be NULL) receives the boundary-flux total;
+ * returns the number of first-order cells, or -1 if an interior cell had
+ * rho <= 0 or p <= 0. */
+static long sweep(const ora_mesh* m, const double* U, const double* Ubase, int predictor, double dt, double* Unew,
+                  double* bflux) {
     int nv = nvars(m);
     long nblk = nblocks(m);
     long nfirst = 0, nbad = 0;
@@ -424,7 +438,7 @@ long ora_step(const ora_mesh* m, const double* U, double dt, double* Unew, doubl
 #pragma omp for schedule(dynamic, 1)
 #endif
         for (long b = 0; b < nblk; ++b)
-            advance_block(m, U, dt, b, Unew, bf_all + b * MAXV, &nfirst, &nbad, &w);
+            advance_block(m, U, Ubase, predictor, dt, b, Unew, bf_all + b * MAXV, &nfirst, &nbad, &w);
         free(w.U); free(w.W); free(w.R); free(w.FS); free(w.first);
     }
     if (bflux) {
@@ -438,11 +452,44 @@ long ora_step(const ora_mesh* m, const double* U, double dt, double* Unew, doubl
     return nbad ? -1 : nfirst;
 }
 
+/* One MUSCL-Hancock time step of every block: Unew = step(U, dt); bflux and
+ * the return value as for sweep(). */
+long ora_step(const ora_mesh* m, const double* U, double dt, double* Unew, double* bflux) {
+    return sweep(m, U, NULL, 1, dt, Unew, bflux);
+}
+
+/* One Runge-Kutta stage with the plain MUSCL operator L (no half step):
+ * Ubase = NULL: Unew = U + dt L(U) (the first Heun stage); else
+ * Unew = 0.5 * (Ubase + (U + dt L(U))) (the second). */
+long ora_stage(const ora_mesh* m, const double* U, const double* Ubase, double dt, double* Unew, double* bflux) {
+    return sweep(m, U, Ubase, 0, dt, Unew, bflux);
+}
+
+/* One step of Heun's two-stage Runge-Kutta method (the strong-stability-
+ * preserving RK2 of Shu and Osher) with the plain MUSCL operator:
+ *   U* = U + dt L(U),   Unew = 0.5 * (U + (U* + dt L(U*))),
+ * guards refreshed from each stage's own state. bflux receives
+ * 0.5 * (B1 + B2) (sum Unew = sum U - bflux); returns the first-order cells of
+ * both stages, or -1 on a non-physical interior state. */
+long ora_step_rk2(const ora_mesh* m, const double* U, double dt, double* Unew, double* bflux) {
+    int nv = nvars(m);
+    size_t n = (size_t)nblocks(m) * nv * ncell_block(m);
+    double* Us = (double*)malloc(sizeof(double) * n);
+    double b1[MAXV], b2[MAXV];
+    long f1 = ora_stage(m, U, NULL, dt, Us, b1);
+    long f2 = (f1 < 0) ? -1 : ora_stage(m, Us, U, dt, Unew, b2);
+    free(Us);
+    if (f1 < 0 || f2 < 0) return -1;
+    if (bflux) for (int v = 0; v < nv; ++v) bflux[v] = 0.5 * (b1[v] + b2[v]);
+    return f1 + f2;
+}
+
 /* nsteps steps in place, each with dt = CFL / max signal speed of the current
  * state; dts (may be NULL) receives each step's dt, bflux_total (may be NULL,
- * nvar doubles) the accumulated boundary fluxes. Returns 0, or -1 if a state
- * became non-physical. */
-int ora_run(const ora_mesh* m, double* U, int nsteps, double* dts, double* bflux_total) {
+ * nvar doubles) the accumulated boundary fluxes. rk2 = 0: MUSCL-Hancock
+ * steps; rk2 = 1: Heun RK2 steps. Returns 0, or -1 if a state became
+ * non-physical. */
+int ora_run_scheme(const ora_mesh* m, double* U, int nsteps, int rk2, double* dts, double* bflux_total) {
     int nv = nvars(m);
     size_t n = (size_t)nblocks(m) * nv * ncell_block(m);
     double* tmp = (double*)malloc(sizeof(double) * n);
@@ -452,7 +499,7 @@ int ora_run(const ora_mesh* m, double* U, int nsteps, double* dts, double* bflux
         double dt = ora_dt(m, U);
         if (!(dt > 0.0)) { rc = -1; break; }
         double bf[MAXV];
-        long nf = ora_step(m, U, dt, tmp, bf);
+        long nf = rk2 ? ora_step_rk2(m, U, dt, tmp, bf) : ora_step(m, U, dt, tmp, bf);
         if (nf < 0) { rc = -1; break; }
         memcpy(U, tmp, sizeof(double) * n);
         if (dts) dts[s] = dt;
@@ -460,4 +507,9 @@ int ora_run(const ora_mesh* m, double* U, int nsteps, double* dts, double* bflux
     }
     free(tmp);
     return rc;
+}
+
+/* nsteps MUSCL-Hancock steps in place (ora_run_scheme with rk2 = 0). */
+int ora_run(const ora_mesh* m, double* U, int nsteps, double* dts, double* bflux_total) {
+    return ora_run_scheme(m, U, nsteps, 0, dts, bflux_total);
 }

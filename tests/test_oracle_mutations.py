@@ -17,6 +17,7 @@ import oracle
 from oracle import build as obuild
 
 from . import test_oracle_pins as pins
+from . import test_oracle_rk2_pins as rk2
 
 MUTATIONS = {
     "drop_dp_over_rho": ("((un * dun) + (dp * rc))", "(un * dun)"),
@@ -39,6 +40,14 @@ MUTATIONS = {
     "outflow_reflects_inner_cell": ("if (gi > n - 1) return n - 1;", "if (gi > n - 1) return n - 2;"),
     "periodic_off_by_one": ("if (periodic) { gi %= n; if (gi < 0) gi += n; return gi; }",
                             "if (periodic) { gi %= n; if (gi < 0) gi += n - 1; return gi; }"),
+    # the Heun RK2 integrator
+    "rk2_forward_euler_twice": ("Unew[o] = Ubase ? (0.5 * (Ubase[o] + us)) : us;", "Unew[o] = us;"),
+    "rk2_stage_weights": ("(0.5 * (Ubase[o] + us))", "((0.25 * Ubase[o]) + (0.75 * us))"),
+    "rk2_boundary_flux_weight": ("bflux[v] = 0.5 * (b1[v] + b2[v]);", "bflux[v] = b1[v] + b2[v];"),
+    "rk2_stages_use_half_step": ("return sweep(m, U, Ubase, 0, dt, Unew, bflux);",
+                                 "return sweep(m, U, Ubase, 1, dt, Unew, bflux);"),
+    "rk2_second_stage_from_old_state": ("long f2 = (f1 < 0) ? -1 : ora_stage(m, Us, U, dt, Unew, b2);",
+                                        "long f2 = (f1 < 0) ? -1 : ora_stage(m, U, Us, dt, Unew, b2);"),
 }
 
 # cheapest first; a mutation is caught as soon as one of them fails
@@ -59,6 +68,11 @@ PIN_TESTS = [
     ("order_acoustic_x", lambda o: pins.test_second_order_on_smooth_acoustic_wave(o, (1, 0))),
     ("order_acoustic_diag", lambda o: pins.test_second_order_on_smooth_acoustic_wave(o, (1, 1))),
     ("order_advection", lambda o: pins.test_second_order_on_advected_density_wave(o)),
+    ("rk2_free_stream", lambda o: rk2.test_rk2_free_stream_is_preserved_bitwise(o, 3, (1, 1, 1))),
+    ("rk2_conservation_bflux", lambda o: rk2.test_rk2_conservation_with_boundary_fluxes(o, "sod")),
+    ("rk2_sod_exact", lambda o: rk2.test_rk2_sod_matches_exact_solution_and_rows_are_identical(o)),
+    ("rk2_order_advection", lambda o: rk2.test_rk2_second_order_on_advected_density_wave(o)),
+    ("rk2_order_acoustic", lambda o: rk2.test_rk2_second_order_on_smooth_acoustic_wave(o)),
 ]
 
 
