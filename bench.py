@@ -8,7 +8,7 @@ per time step guard fill + hydro task on every packet + dt reduction, and
 unpack the result. Metric: zone-updates/s (interior cells x time steps / s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff]
+                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff|sedov128_rk2]
                     [--no-cpu-baseline]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 # once per zone (add, sub, mul, div, sqrt each 1): primitives 12, slopes 15,
 # predictor 64, face states 45, HLL 3 x 86, update 45, signal speed 23.
 FLOPS_PER_ZONE_3D = 462
+# A Heun RK2 step: two plain-MUSCL stages (primitives 12, slopes 15, face
+# states 45, HLL 3 x 86, update 45 each), the signal speed once (23) and the
+# stage combination 0.5 (U + U*) (10).
+FLOPS_PER_ZONE_3D_RK2 = 2 * (12 + 15 + 45 + 3 * 86 + 45) + 23 + 10
 BYTES_PER_ZONE_3D = 80        # read U^n and write U^{n+1}: 5 vars x 8 B x 2
 FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 2032 MHz, non-FMA ops
 
@@ -73,7 +77,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sedov128",
-                    choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff"])
+                    choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff",
+                             "sedov128_rk2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -90,12 +95,17 @@ def workload(name):
         desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
         nt = 10
     task = "f32flux" if name.endswith("_f32") else "ff" if name.endswith("_ff") else "fp64"
+    if name.endswith("_rk2"):
+        import dataclasses
+        task = "rk2"
+        spec = dataclasses.replace(spec, cfl=0.4)
+        desc += "; Heun RK2 steps (two plain-MUSCL stages), CFL 0.4"
     return spec, packets, nt, task, desc
 
 
 DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 update",
-          "ff": "double-word f32x2 reconstruction/flux + f64 update"}
-KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw"}
+          "ff": "double-word f32x2 reconstruction/flux + f64 update", "rk2": "f64"}
+KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw", "rk2": "rd,true"}
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -267,7 +277,7 @@ def main():
     batch = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
     hydro_events = []
     # per bench step: pack, signal speed (one launch), dt reduce, nt persistent launches, unpack
-    launches_per_step = 1 + 1 + 1 + nt + 1
+    launches_per_step = 1 + 1 + 1 + nt * (2 if task_name == "rk2" else 1) + 1
 
     def step(record: bool):
         B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
@@ -323,15 +333,17 @@ def main():
     avg_launch_s = tot_s / len(durs)
     zones_per_launch = tot_zones / len(durs)
     hydro_share = tot_s / (ms * 1e-3)
-    fp64_bound = task_name == "fp64"
+    fp64_bound = task_name in ("fp64", "rk2")
     if fp64_bound:
-        achieved = FLOPS_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e12
-        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},rd>"
+        flops = FLOPS_PER_ZONE_3D_RK2 if task_name == "rk2" else FLOPS_PER_ZONE_3D
+        achieved = flops * zones_per_launch / avg_launch_s / 1e12
+        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
         traffic = (profiled_traffic("persistent_kernel_fp64_sedov128.md", kname)
                    if args.workload == "sedov128" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": kname, "per_launch": "one time step of all packets",
+                "kernel": kname, "per_launch": "one time step of all packets" + (
+                    " (two stage launches)" if task_name == "rk2" else ""),
                 "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
     else:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(

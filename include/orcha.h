@@ -104,7 +104,22 @@ typedef enum {
      * differences are double-word, the conservative update, the guard fill
      * and the dt reduction FP64. Not in the paper: a variant of its task
      * for a GPU whose FP64 rate is a small fraction of its FP32 rate. */
-    ORCHA_TASK_HYDRO_FF = 4
+    ORCHA_TASK_HYDRO_FF = 4,
+    /* The first stage of Heun's two-stage Runge-Kutta step (the paper's
+     * Spark solver is explicit finite volume with 2nd-order Runge-Kutta,
+     * section "Experiments") with the plain MUSCL operator L (minmod slopes
+     * of the primitives, face states W -+ dW/2, no half step, HLL), FP64:
+     * other buffer = current + dt L(current). Raises no signal speed. */
+    ORCHA_TASK_RK2_STAGE1 = 5,
+    /* The second stage: other buffer = 0.5 * (other + (current + dt L(current))),
+     * i.e. with the stage-1 state current (after a swap) and the step's
+     * initial state in the other buffer, the new state replaces the initial
+     * one. Raises the blocks' signal speeds of the new state. The guard fill
+     * must refresh the current (stage-1) buffer before it. */
+    ORCHA_TASK_RK2_STAGE2 = 6,
+    /* For orcha_mesh_advance, orcha_batch_advance and orcha_autotune: whole
+     * Heun steps (stage 1, swap, guard fill, stage 2, dt reduce, swap). */
+    ORCHA_TASK_HYDRO_RK2 = 7
 } orcha_task;
 
 /* Mesh geometry and the caller's device buffers. */

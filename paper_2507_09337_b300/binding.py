@@ -34,12 +34,16 @@ ORCHA_TASK_HYDRO_FP64 = 1
 ORCHA_TASK_HYDRO_F32FLUX = 2
 ORCHA_TASK_SIGNAL_SPEED = 3
 ORCHA_TASK_HYDRO_FF = 4
+ORCHA_TASK_RK2_STAGE1 = 5
+ORCHA_TASK_RK2_STAGE2 = 6
+ORCHA_TASK_HYDRO_RK2 = 7
 
 ORCHA_INIT_FROM_HOST = 0
 ORCHA_INIT_SPHERE = 1
 ORCHA_INIT_HALF_SPACE = 2
 
-TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF}
+TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF,
+         "rk2": ORCHA_TASK_HYDRO_RK2}
 
 
 class OrchaError(RuntimeError):

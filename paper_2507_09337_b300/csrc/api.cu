@@ -334,7 +334,10 @@ orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
         case ORCHA_TASK_HYDRO_FP64:
         case ORCHA_TASK_HYDRO_F32FLUX:
         case ORCHA_TASK_HYDRO_FF:
-            e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, orcha::prec_of(task), p->ids_dev, p->n, cur, nxt, st);
+        case ORCHA_TASK_RK2_STAGE1:
+        case ORCHA_TASK_RK2_STAGE2:
+            e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, orcha::prec_of(task), p->ids_dev, p->n, cur, nxt,
+                                    orcha::stage_of(task), st);
             break;
         case ORCHA_TASK_SIGNAL_SPEED: e = orcha::launch_signal_speed(m->dev, p->ids_dev, p->n, cur, st); break;
         default: return fail(ORCHA_ERR_INVALID, "packet_run: unknown task %d", (int)task);
@@ -359,13 +362,20 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
                    "advance signal speed");
         if ((s = orcha_dt_reduce(m, stream))) return s;
     }
+    // a Heun step is two sweeps (stage 1, swap, stage 2, swap), every other
+    // step one; each sweep refreshes the guards of the state it reads
+    const bool rk = task == ORCHA_TASK_HYDRO_RK2;
+    const orcha_task sweeps[2] = {rk ? ORCHA_TASK_RK2_STAGE1 : task, ORCHA_TASK_RK2_STAGE2};
     for (int n = 0; n < nsteps; ++n) {
-        for (int i = 0; i < npk; ++i)
-            if ((s = orcha_packet_run(pk[i], ORCHA_TASK_GUARD_FILL, stream))) return s;
-        for (int i = 0; i < npk; ++i)
-            if ((s = orcha_packet_run(pk[i], task, stream))) return s;
-        if ((s = orcha_dt_reduce(m, stream))) return s;
-        m->cur ^= 1;
+        for (int k = 0; k < (rk ? 2 : 1); ++k) {
+            for (int i = 0; i < npk; ++i)
+                if ((s = orcha_packet_run(pk[i], ORCHA_TASK_GUARD_FILL, stream))) return s;
+            for (int i = 0; i < npk; ++i)
+                if ((s = orcha_packet_run(pk[i], sweeps[k], stream))) return s;
+            if (!rk || k == 1)
+                if ((s = orcha_dt_reduce(m, stream))) return s;
+            m->cur ^= 1;
+        }
     }
     return ORCHA_OK;
 }
@@ -373,8 +383,8 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
 orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t npk, orcha_task task, int32_t nsteps,
                                 int32_t init_dt, int32_t use_graph, void* stream) {
     if (!m || (!pk && npk > 0) || npk < 0 || nsteps < 0) return fail(ORCHA_ERR_INVALID, "mesh_advance: bad argument");
-    if (orcha::prec_of(task) < 0)
-        return fail(ORCHA_ERR_INVALID, "mesh_advance: task must be a hydro task");
+    if (!orcha::is_step_task(task))
+        return fail(ORCHA_ERR_INVALID, "mesh_advance: task must be a whole-step hydro task");
     long long covered = 0;
     for (int i = 0; i < npk; ++i) {
         if (!pk[i] || pk[i]->mesh != m) return fail(ORCHA_ERR_INVALID, "mesh_advance: packet %d not of this mesh", i);
@@ -391,7 +401,7 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
         if (g.task == task && g.nsteps == nsteps && g.init_dt == init_dt && g.start_cur == start &&
             g.packets.size() == (size_t)npk && std::equal(g.packets.begin(), g.packets.end(), pk)) {
             ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
-            m->cur = start ^ (nsteps & 1);
+            m->cur = start ^ ((task == ORCHA_TASK_HYDRO_RK2 ? 0 : nsteps) & 1);
             return ORCHA_OK;
         }
     }
@@ -413,7 +423,7 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     m->graphs.push_back(g);
     ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
-    m->cur = start ^ (nsteps & 1);
+    m->cur = start ^ ((task == ORCHA_TASK_HYDRO_RK2 ? 0 : nsteps) & 1);
     return ORCHA_OK;
 }
 
@@ -574,11 +584,14 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
 static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, cudaStream_t st) {
     const int prec = orcha::prec_of(task);
     const orcha_batch::List& L = b->lists[prec];
+    const int stages = task == ORCHA_TASK_HYDRO_RK2 ? 2 : 1;     // a Heun step is two launches
     for (int n = 0; n < nsteps; ++n) {
-        ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
-        ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, prec, L.slots_dev, L.items_dev, L.nitems, b->queue,
-                                            L.grid, st),
-                   "batch launch");
+        for (int k = 1; k <= stages; ++k) {
+            ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
+            ORCHA_CUDA(orcha::launch_persistent(b->ndim, b->tx, b->ty, prec, L.slots_dev, L.items_dev, L.nitems,
+                                                b->queue, L.grid, stages == 2 ? k : 0, st),
+                       "batch launch");
+        }
     }
     return ORCHA_OK;
 }
@@ -586,8 +599,8 @@ static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nst
 orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps, int32_t init_dt, int32_t use_graph,
                                  void* stream) {
     if (!b || nsteps < 0) return fail(ORCHA_ERR_INVALID, "batch_advance: bad argument");
-    if (orcha::prec_of(task) < 0)
-        return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a hydro task");
+    if (!orcha::is_step_task(task))
+        return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a whole-step hydro task");
     cudaStream_t st = (cudaStream_t)stream;
     orcha_status s;
     if ((s = ensure_list(b, orcha::prec_of(task)))) return s;
@@ -626,7 +639,8 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
         }
         ORCHA_CUDA(cudaGraphLaunch(exec, st), "batch graph launch");
     }
-    for (auto* m : b->meshes) m->cur ^= (nsteps & 1);
+    const int flips = nsteps * (task == ORCHA_TASK_HYDRO_RK2 ? 2 : 1);     // one per launch
+    for (auto* m : b->meshes) m->cur ^= (flips & 1);
     return ORCHA_OK;
 }
 

@@ -246,10 +246,16 @@ struct Tile {
 // source cell (a neighbour's interior, or the boundary rule's cell), so no
 // guard-fill pass and no guard storage traffic are needed; the values are
 // the same copies the guard fill would make.
-template <int NDIM, int TX, int TY, class T, bool GATHER>
+//
+// RK = true: one stage of Heun's two-stage Runge-Kutta method with the plain
+// MUSCL operator L (face states from the stage's own primitives, no half
+// step). stage 1: Uout = Uin + dt L(Uin); stage 2: Uout = 0.5 * (Uout +
+// (Uin + dt L(Uin))), the old Uout (the step's initial state) read at the
+// cell just before it is overwritten. Stage 1 raises no signal speed.
+template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false>
 __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
                                              const double* __restrict__ Uin, double* __restrict__ Uout,
-                                             unsigned char* smem_raw, int z0 = 0, int z1 = -1) {
+                                             unsigned char* smem_raw, int z0 = 0, int z1 = -1, int stage = 0) {
     using Tl = Tile<NDIM, TX, TY>;
     using S = typename P<T>::store;
     constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
@@ -409,6 +415,11 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 const A dr = as<A>(P<T>::ld(&wp[v * R2N + cp])) - Wc[v];
                 dW[d][v] = minmod(dl, dr);
             }
+        }
+        if constexpr (RK) {                      // plain MUSCL: face states about Wc itself
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Wb[v] = Wc[v];
+            return;
         }
         const A gp = as<A>(g) * Wc[NV - 1];
 #pragma unroll
@@ -628,10 +639,11 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                         const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
                         const rd acc = rd(acc_prev[v]) + tz;
                         Un[v] = rd(Ub[gi + v * vs]) - acc;
+                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     }
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
@@ -664,10 +676,13 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 for (int v = 0; v < NV; ++v) {
                     if constexpr (F32) Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(acc_ff[v]));
                     else if constexpr (DW) Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v]));
-                    else Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
+                    else {
+                        Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
+                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
+                    }
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
             }
         }
     }
@@ -676,18 +691,18 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 
 // Packet path: one CTA per (packet block, column tile); guards come from the
 // padded block.
-template <int NDIM, int TX, int TY, class T>
+template <int NDIM, int TX, int TY, class T, bool RK = false>
 __global__ void __launch_bounds__(TX * TY)
 hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
-             const double* __restrict__ Uin, double* __restrict__ Uout) {
+             const double* __restrict__ Uin, double* __restrict__ Uout, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[32];
     const int ntile = tiles_x * tiles_y;
     const int blk = blk_ids[blockIdx.x / ntile];
     const int tile = blockIdx.x % ntile;
-    const double s = hydro_tile<NDIM, TX, TY, T, false>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
-                                                        Uin, Uout, smem_raw);
-    cta_raise_smax(s, red, &m.smax[blk]);
+    const double s = hydro_tile<NDIM, TX, TY, T, false, RK>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
+                                                            Uin, Uout, smem_raw, 0, -1, stage);
+    if (!RK || stage == 2) cta_raise_smax(s, red, &m.smax[blk]);     // uniform over the CTA
 }
 
 }  // namespace orcha

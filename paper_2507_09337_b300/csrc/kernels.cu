@@ -400,52 +400,56 @@ cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigne
 }
 
 // ---------------------------------------------------------------- hydro launch table
-template <int NDIM, int TX, int TY, class T>
+// Variant of a precision code: arithmetic type and whether the kernel runs
+// Runge-Kutta stages (kRK2: FP64, plain MUSCL).
+template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,
-                                  cudaStream_t st) {
+                                  int stage, cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    auto kern = hydro_kernel<NDIM, TX, TY, T>;
+    auto kern = hydro_kernel<NDIM, TX, TY, T, RK>;
     const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
-    kern<<<dim3((unsigned)(n * tx * ty)), dim3(TX * TY), smem, st>>>(m, ids, tx, ty, Uin, Uout);
+    kern<<<dim3((unsigned)(n * tx * ty)), dim3(TX * TY), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage);
     return cudaGetLastError();
 }
 
-template <int NDIM, int TX, int TY, class T>
+template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t configure_t() {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    cudaError_t e = cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T, RK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(persistent_kernel<NDIM, TX, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(persistent_kernel<NDIM, TX, TY, T, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 
-template <int NDIM, int TX, int TY, class T>
+template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t launch_persistent_t(const SlotDev* slots, const Item* items, int nitems, unsigned* queue, int grid,
-                                       cudaStream_t st) {
+                                       int stage, cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    persistent_kernel<NDIM, TX, TY, T><<<grid, TX * TY, smem, st>>>(slots, items, nitems, queue);
+    persistent_kernel<NDIM, TX, TY, T, RK><<<grid, TX * TY, smem, st>>>(slots, items, nitems, queue, stage);
     return cudaGetLastError();
 }
 
-template <int NDIM, int TX, int TY, class T>
+template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t occupancy_t(int* per_sm) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T>, TX * TY, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T, RK>, TX * TY,
+                                                         smem);
 }
 
-#define ORCHA_PERS_CASE(ND, X, Y)                                                                      \
-    if (ndim == ND && tx == X && ty == Y)                                                              \
-        return prec == kF32  ? launch_persistent_t<ND, X, Y, float>(slots, items, nitems, queue, grid, st) \
-               : prec == kFF ? launch_persistent_t<ND, X, Y, dw>(slots, items, nitems, queue, grid, st)    \
-                             : launch_persistent_t<ND, X, Y, rd>(slots, items, nitems, queue, grid, st);
+#define ORCHA_PERS_CASE(ND, X, Y)                                                                         \
+    if (ndim == ND && tx == X && ty == Y)                                                                 \
+        return prec == kF32   ? launch_persistent_t<ND, X, Y, float, false>(slots, items, nitems, queue, grid, 0, st) \
+               : prec == kFF  ? launch_persistent_t<ND, X, Y, dw, false>(slots, items, nitems, queue, grid, 0, st)    \
+               : prec == kRK2 ? launch_persistent_t<ND, X, Y, rd, true>(slots, items, nitems, queue, grid, stage, st) \
+                              : launch_persistent_t<ND, X, Y, rd, false>(slots, items, nitems, queue, grid, 0, st);
 
 cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
-                              int nitems, unsigned* queue, int grid, cudaStream_t st) {
+                              int nitems, unsigned* queue, int grid, int stage, cudaStream_t st) {
     ORCHA_PERS_CASE(2, 8, 8)
     ORCHA_PERS_CASE(2, 16, 8)
     ORCHA_PERS_CASE(2, 16, 16)
@@ -457,9 +461,10 @@ cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev*
 
 #define ORCHA_OCC_CASE(ND, X, Y)                                                                       \
     if (ndim == ND && tx == X && ty == Y)                                                              \
-        return prec == kF32  ? occupancy_t<ND, X, Y, float>(per_sm)                                    \
-               : prec == kFF ? occupancy_t<ND, X, Y, dw>(per_sm)                                       \
-                             : occupancy_t<ND, X, Y, rd>(per_sm);
+        return prec == kF32   ? occupancy_t<ND, X, Y, float, false>(per_sm)                            \
+               : prec == kFF  ? occupancy_t<ND, X, Y, dw, false>(per_sm)                               \
+               : prec == kRK2 ? occupancy_t<ND, X, Y, rd, true>(per_sm)                                \
+                              : occupancy_t<ND, X, Y, rd, false>(per_sm);
 
 cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm) {
     ORCHA_OCC_CASE(2, 8, 8)
@@ -473,12 +478,13 @@ cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm
 
 #define ORCHA_TILE_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y)                                                              \
-        return prec == kF32  ? launch_hydro_t<ND, X, Y, float>(m, ids, n, Uin, Uout, st)               \
-               : prec == kFF ? launch_hydro_t<ND, X, Y, dw>(m, ids, n, Uin, Uout, st)                  \
-                             : launch_hydro_t<ND, X, Y, rd>(m, ids, n, Uin, Uout, st);
+        return prec == kF32   ? launch_hydro_t<ND, X, Y, float, false>(m, ids, n, Uin, Uout, 0, st)    \
+               : prec == kFF  ? launch_hydro_t<ND, X, Y, dw, false>(m, ids, n, Uin, Uout, 0, st)       \
+               : prec == kRK2 ? launch_hydro_t<ND, X, Y, rd, true>(m, ids, n, Uin, Uout, stage, st)    \
+                              : launch_hydro_t<ND, X, Y, rd, false>(m, ids, n, Uin, Uout, 0, st);
 
 cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
-                         double* Uout, cudaStream_t st) {
+                         double* Uout, int stage, cudaStream_t st) {
     const int ndim = m.ndim;
     ORCHA_TILE_CASE(2, 8, 8)
     ORCHA_TILE_CASE(2, 16, 8)
@@ -491,9 +497,10 @@ cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* 
 
 #define ORCHA_CONF_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y) {                                                            \
-        cudaError_t e = configure_t<ND, X, Y, float>();                                                \
-        if (e == cudaSuccess) e = configure_t<ND, X, Y, dw>();                                         \
-        return e != cudaSuccess ? e : configure_t<ND, X, Y, rd>();                                     \
+        cudaError_t e = configure_t<ND, X, Y, float, false>();                                         \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, dw, false>();                                  \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, rd, true>();                                   \
+        return e != cudaSuccess ? e : configure_t<ND, X, Y, rd, false>();                              \
     }
 
 cudaError_t configure_hydro(int ndim, int tx, int ty) {

@@ -9,13 +9,31 @@
 
 namespace orcha {
 
-// Arithmetic variants of the hydro kernels: FP64, FP32 reconstruction/flux,
-// double-word reconstruction/flux (all with the FP64 update).
-enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2 };
-constexpr int kNumPrec = 3;
+// Variants of the hydro kernels: MUSCL-Hancock steps in FP64, with FP32
+// reconstruction/flux or with double-word reconstruction/flux (all with the
+// FP64 update), and Heun Runge-Kutta stages (plain MUSCL, FP64).
+enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3 };
+constexpr int kNumPrec = 4;
 // Variant of a hydro task, or -1 for any other task.
 inline int prec_of(orcha_task t) {
-    return t == ORCHA_TASK_HYDRO_FP64 ? kF64 : t == ORCHA_TASK_HYDRO_F32FLUX ? kF32 : t == ORCHA_TASK_HYDRO_FF ? kFF : -1;
+    switch (t) {
+        case ORCHA_TASK_HYDRO_FP64: return kF64;
+        case ORCHA_TASK_HYDRO_F32FLUX: return kF32;
+        case ORCHA_TASK_HYDRO_FF: return kFF;
+        case ORCHA_TASK_HYDRO_RK2:
+        case ORCHA_TASK_RK2_STAGE1:
+        case ORCHA_TASK_RK2_STAGE2: return kRK2;
+        default: return -1;
+    }
+}
+// Runge-Kutta stage of a packet task (1 or 2), 0 for a whole-step task.
+inline int stage_of(orcha_task t) {
+    return t == ORCHA_TASK_RK2_STAGE1 ? 1 : t == ORCHA_TASK_RK2_STAGE2 ? 2 : 0;
+}
+// Tasks that advance whole steps (mesh_advance, batch_advance, autotune).
+inline bool is_step_task(orcha_task t) {
+    return t == ORCHA_TASK_HYDRO_FP64 || t == ORCHA_TASK_HYDRO_F32FLUX || t == ORCHA_TASK_HYDRO_FF ||
+           t == ORCHA_TASK_HYDRO_RK2;
 }
 
 // Error reporting of the C ABI (sets the calling thread's orcha_last_error).
@@ -25,8 +43,10 @@ orcha_status cuda_error(cudaError_t e, const char* what);
 // left null). Host-only.
 orcha_status mesh_dev_from_desc(const orcha_mesh_desc* d, MeshDev* out, long long* nblk_out);
 
+// One hydro launch over the packet blocks ids[0..n); stage: Runge-Kutta stage
+// (1 or 2) for kRK2, else 0.
 cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
-                         double* Uout, cudaStream_t st);
+                         double* Uout, int stage, cudaStream_t st);
 bool hydro_tile_supported(int ndim, int tx, int ty);
 // Set the dynamic shared-memory limit of every precision of a tile variant on
 // the current device (call once per device before launching or capturing).
@@ -67,7 +87,7 @@ cudaError_t launch_selftest_dword(unsigned long long n, unsigned long long seed,
 constexpr int kTiles[3][2] = {{16, 16}, {16, 8}, {8, 8}};
 // One persistent launch (one time step of every mesh in `slots`).
 cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
-                              int nitems, unsigned* queue, int grid, cudaStream_t st);
+                              int nitems, unsigned* queue, int grid, int stage, cudaStream_t st);
 // Resident CTAs per SM of a persistent variant.
 cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm);
 

@@ -40,9 +40,11 @@ struct Item {
     int slot, blk, tile, zr;
 };
 
-// Finish a mesh's step: dt = cfl / max signal speed, clear the maxima and the
-// item counter, flip the current buffer. Called by all threads of one CTA.
-__device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red) {
+// Finish a mesh's step: dt = cfl / max signal speed (unless update_dt is
+// false: the first stage of a Runge-Kutta step keeps dt), clear the maxima
+// and the item counter, flip the current buffer. Called by all threads of
+// one CTA.
+__device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red, bool update_dt) {
     unsigned long long b = 0;
     for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) b = umax64(b, __ldcg(&sd.m.smax[i]));
     b = warp_max_u64(b);
@@ -53,8 +55,10 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
         unsigned long long t = 0;
         for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t = umax64(t, red[w]);
         const double s = __longlong_as_double((long long)t);
-        if (s > 0.0 && s <= 1.7976931348623157e308) *sd.dt = sd.m.cfl / s;
-        else atomicOr(sd.m.err, 2);
+        if (update_dt) {
+            if (s > 0.0 && s <= 1.7976931348623157e308) *sd.dt = sd.m.cfl / s;
+            else atomicOr(sd.m.err, 2);
+        }
         *sd.done = 0u;
         *sd.cur ^= 1;
     }
@@ -71,10 +75,12 @@ template <class T, int NT> struct MinBlocks { static constexpr int value = (512 
 template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 
-template <int NDIM, int TX, int TY, class T>
+// RK = true: the launch is Runge-Kutta stage `stage` (1 or 2) of every mesh
+// (hydro_tile); the first stage leaves dt as it is.
+template <int NDIM, int TX, int TY, class T, bool RK = false>
 __global__ void __launch_bounds__(TX * TY, (MinBlocks<T, TX * TY>::value))
 persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ items, int nitems,
-                  unsigned int* __restrict__ queue) {
+                  unsigned int* __restrict__ queue, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[32];
     __shared__ int s_item, s_last;
@@ -87,10 +93,10 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         const SlotDev& sd = slots[w.slot];
         const int cur = __ldcg(sd.cur);
         const int z0 = w.zr ? (w.zr & 0xFF) : 0, z1 = w.zr ? (w.zr >> 8) : -1;
-        const double s = hydro_tile<NDIM, TX, TY, T, true>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
-                                                           (w.tile / sd.tiles_x) * TY, sd.state[cur],
-                                                           sd.state[cur ^ 1], smem_raw, z0, z1);
-        cta_raise_smax(s, red, &sd.m.smax[w.blk]);
+        const double s = hydro_tile<NDIM, TX, TY, T, true, RK>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
+                                                               (w.tile / sd.tiles_x) * TY, sd.state[cur],
+                                                               sd.state[cur ^ 1], smem_raw, z0, z1, stage);
+        if (!RK || stage == 2) cta_raise_smax(s, red, &sd.m.smax[w.blk]);     // uniform over the CTA
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned d = atomicAdd(sd.done, 1u);
@@ -99,7 +105,7 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         __syncthreads();
         if (s_last) {
             __threadfence();
-            finish_mesh_step(sd, red);
+            finish_mesh_step(sd, red, !RK || stage == 2);
         }
         __syncthreads();
     }

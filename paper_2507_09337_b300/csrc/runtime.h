@@ -54,7 +54,7 @@ struct orcha_batch {
         orcha::Item* items_dev = nullptr;
         orcha::SlotDev* slots_dev = nullptr;
         unsigned* done_dev = nullptr;
-    } lists[3];
+    } lists[4];                                      // indexed by orcha::Prec (kNumPrec = 4)
     unsigned* queue = nullptr;
     int* cur_dev = nullptr;
     int num_sms = 0;

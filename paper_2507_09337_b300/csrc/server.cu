@@ -116,11 +116,12 @@ struct Req {
 // One launch per (ndim 2 or 3) x (FP64, FP32 flux or FF) x (tile 8x8 or
 // 16x8): blocks of 16 or more cells across x use the 16x8 tile (the
 // autotuner's choice for 16^3 blocks on a B300), 8-cell blocks the 8x8 one.
-constexpr int kGroups = 2 * orcha::kNumPrec * 2;
+constexpr int kServePrec = 3;        // kF64, kF32, kFF (Runge-Kutta steps are not served)
+constexpr int kGroups = 2 * kServePrec * 2;
 __host__ __device__ constexpr int group_ndim(int g) { return 2 + (g & 1); }
-__host__ __device__ constexpr int group_prec(int g) { return (g >> 1) % orcha::kNumPrec; }
-__host__ __device__ constexpr int group_tx(int g) { return (g >> 1) / orcha::kNumPrec ? 16 : 8; }
-constexpr int group_of(int ndim, int prec, int tx) { return (ndim - 2) | ((prec + (tx == 16 ? orcha::kNumPrec : 0)) << 1); }
+__host__ __device__ constexpr int group_prec(int g) { return (g >> 1) % kServePrec; }
+__host__ __device__ constexpr int group_tx(int g) { return (g >> 1) / kServePrec ? 16 : 8; }
+constexpr int group_of(int ndim, int prec, int tx) { return (ndim - 2) | ((prec + (tx == 16 ? kServePrec : 0)) << 1); }
 static_assert(group_of(group_ndim(11), group_prec(11), group_tx(11)) == 11, "group index round trip");
 
 struct GroupBuf {                    // host/device work list of one launch
@@ -300,7 +301,7 @@ bool orcha_server::launch_step(bool* launched) {
         SRV_CUDA(cudaMemsetAsync(g.queue_d, 0, sizeof(unsigned), compute), "step queue");
         const int grid = std::max(1, std::min((int)g.items_h.size(), occ[gi] * num_sms));
         SRV_CUDA(orcha::launch_persistent(ndim, gtx, gty, prec, g.slots_d, g.items_d, (int)g.items_h.size(),
-                                          g.queue_d, grid, compute), "step launch");
+                                          g.queue_d, grid, 0, compute), "step launch");
         for (Req* r : grp) {
             r->cur_host ^= 1;
             if (--r->steps_left == 0) finished.push_back(r);
@@ -486,8 +487,8 @@ orcha_status orcha_server_destroy(orcha_server* s) {
 orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, int64_t* ticket) {
     if (!s || !rd || !ticket) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: null argument");
     if (rd->nsteps < 1) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: nsteps < 1");
-    if (orcha::prec_of((orcha_task)rd->task) < 0)
-        return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: task must be a hydro task");
+    if (rd->task != ORCHA_TASK_HYDRO_FP64 && rd->task != ORCHA_TASK_HYDRO_F32FLUX && rd->task != ORCHA_TASK_HYDRO_FF)
+        return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: task must be HYDRO_FP64, HYDRO_F32FLUX or HYDRO_FF");
     if (rd->init_kind == ORCHA_INIT_FROM_HOST && !rd->init_host)
         return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: FROM_HOST needs init_host");
     if (rd->init_kind == ORCHA_INIT_HALF_SPACE && (rd->region[0] < 0 || rd->region[0] >= rd->ndim))

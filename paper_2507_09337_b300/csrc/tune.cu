@@ -63,8 +63,8 @@ bool write_cache(const char* path, const Cache& c) {
 extern "C" orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_task task, int32_t nblocks,
                                        const char* cache_path, int32_t* tx_out, int32_t* ty_out, double* ms_out) {
     if (!bs || !tx_out || !ty_out) return orcha::set_error(ORCHA_ERR_INVALID, "autotune: null argument");
-    if (orcha::prec_of(task) < 0)
-        return orcha::set_error(ORCHA_ERR_INVALID, "autotune: task must be a hydro task");
+    if (!orcha::is_step_task(task))
+        return orcha::set_error(ORCHA_ERR_INVALID, "autotune: task must be a whole-step hydro task");
     if (nblocks < 1 || nblocks > (1 << 16)) return orcha::set_error(ORCHA_ERR_INVALID, "autotune: nblocks in [1, 65536]");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -61,9 +61,9 @@ def gpu_steps(spec, U0, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, packets=None, tile
         mesh.close()
 
 
-def oracle_steps(oracle_mod, spec, U0, nsteps):
+def oracle_steps(oracle_mod, spec, U0, nsteps, rk2=False):
     m = oracle_mod.Mesh(**spec.oracle_kwargs())
-    U, dts, _ = oracle_mod.run(m, U0, nsteps)
+    U, dts, _ = oracle_mod.run(m, U0, nsteps, rk2=rk2)
     return U, dts
 
 
