@@ -146,6 +146,14 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     } else if (P<AS>::le0(SR)) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FR[v];
+    } else if constexpr (kContract && std::is_same<AC, rd>::value) {
+        // the same flux as F_L + k ((F_L - F_R) + S_R (U_R - U_L)), k = S_L / (S_R - S_L):
+        // four FP64 operations per variable instead of five
+        const rd sl = SL, sr = SR;
+        const rd k = sl * P<rd>::rcp(sr - sl);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            F[v] = rd(fma(k.v, fma(sr.v, (UR[v] - UL[v]).v, (FL[v] - FR[v]).v), FL[v].v));
     } else {
         const AC sl = as<AC>(SL), sr = as<AC>(SR);
         const AC slsr = sl * sr;
