@@ -316,7 +316,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     // the source column. Per plane only the z part is added (uniform over the
     // CTA). GATHER = false reads the padded block itself.
     constexpr int KMAX = (R2N + NT - 1) / NT;
-    long long base_xy[KMAX];
+    int bxy[KMAX], oxy[KMAX];             // source block's (x, y) index; in-block offset of the column
     unsigned interior_mask = 0;           // bit k: cell k is an interior column of the tile
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
@@ -339,15 +339,19 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             }
             sbx = sb[0]; sby = sb[1]; sx = sl[0]; sy = sl[1];
         }
-        base_xy[k] = (sbx + (long long)m.nb[0] * sby) * m.blk_stride + ((long long)sy * px + sx);
+        bxy[k] = sbx + m.nb[0] * sby;
+        oxy[k] = sy * px + sx;
         if (ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2) interior_mask |= 1u << k;
     }
-    const long long nbxy_stride = (long long)m.nb[0] * m.nb[1] * m.blk_stride;
-    const long long plane = (long long)py * px;
+    const int nbxy = m.nb[0] * m.nb[1];
+    const int plane = py * px;
 
-    // z part of the source offset of plane pzi (interior z index, -2 .. bz+1; 2D: 0)
-    auto plane_zoff = [&](int pzi) -> long long {
-        if (NDIM != 3) return 0;
+    // z part of the source of plane pzi (interior z index, -2 .. bz+1; 2D: 0):
+    // the block-index offset (zb) and the in-block cell offset (zc)
+    auto plane_z = [&](int pzi, int& zb, int& zc) {
+        zb = 0;
+        zc = 0;
+        if (NDIM != 3) return;
         int sbz = bc[2], sz = pzi + kGuard;
         if (GATHER && (pzi < 0 || pzi >= bz)) {
             const int n = m.nb[2] * m.bs[2];
@@ -357,15 +361,21 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             sbz = gi / m.bs[2];
             sz = gi % m.bs[2] + kGuard;
         }
-        return sbz * nbxy_stride + sz * plane;
+        zb = sbz * nbxy;
+        zc = sz * plane;
+    };
+    // source of R2 cell k of this thread in the plane with z part (zb, zc)
+    auto src_of = [&](int k, int zb, int zc) -> const double* {
+        return Uin + (long long)(bxy[k] + zb) * m.blk_stride + (oxy[k] + zc);
     };
     // Ask L2 for the source lines of plane pzi ahead of its load (no registers held).
     auto prefetch_plane = [&](int pzi) {
-        const long long zoff = plane_zoff(pzi);
+        int zb, zc;
+        plane_z(pzi, zb, zc);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             if (tid + k * NT >= R2N) break;
-            const double* src = Uin + base_xy[k] + zoff;
+            const double* src = src_of(k, zb, zc);
 #pragma unroll
             for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + v * vs));
         }
@@ -374,13 +384,14 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     auto load_plane = [&](int pzi) {
         const int slot = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
         S* w = sW + slot * NW * R2N;
-        const long long zoff = plane_zoff(pzi);
+        int zb, zc;
+        plane_z(pzi, zb, zc);
         const bool zin = pzi >= 0 && pzi < bz;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int c = tid + k * NT;
             if (c >= R2N) break;
-            const double* src = Uin + base_xy[k] + zoff;
+            const double* src = src_of(k, zb, zc);
             T U[NV], W[NV], r;
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[v] = P<T>::in(src[v * vs]);

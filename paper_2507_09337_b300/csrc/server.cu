@@ -262,7 +262,7 @@ bool orcha_server::launch_step(bool* launched) {
         if (grp.empty()) continue;
         for (size_t i = 0; i < grp.size(); ++i) {
             Req* r = grp[i];
-            orcha::SlotDev sd;
+            orcha::SlotDev sd{};
             sd.m = r->m;
             sd.state[0] = r->state[0];
             sd.state[1] = r->state[1];
