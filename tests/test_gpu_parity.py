@@ -209,3 +209,31 @@ def test_integer_pipe_fp64_arithmetic_matches_hardware():
     """The integer-pipe binary64 add/sub/mul give the hardware's bits on 2^31
     pseudo-random operand pairs (carries, ties, cancellation, zeros)."""
     assert B.orcha_selftest_fp64_emulation(1 << 31, seed=2024) == 0
+
+
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_FF,
+                                  B.ORCHA_TASK_HYDRO_RK2])
+@pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1)])
+def test_free_stream_is_preserved_bitwise(task, periodic):
+    """A uniform state with an arbitrary velocity is the degenerate case of the
+    scheme: every slope is zero and both faces of a cell carry the same flux,
+    so every variant keeps it bit for bit, through the packet path and the
+    persistent path."""
+    rng = np.random.default_rng(3)
+    spec = wl.MeshSpec(ndim=3, nb=(2, 2, 2), bs=(16, 16, 16), periodic=periodic)
+    U0 = wl.uniform_state(spec, rng.uniform(0.5, 2), rng.uniform(-1, 1, 3), rng.uniform(0.5, 2))
+    G, _, err = gpu_steps(spec, U0, 4, task=task)
+    assert err == 0 and np.array_equal(G, U0)
+    from .gpu_helpers import gpu_batch_steps
+    (H,), errs = gpu_batch_steps([(spec, U0, None)], 4, task=task)
+    assert errs == [0] and np.array_equal(H, U0)
+
+
+def test_nonphysical_state_is_reported_by_the_batch_path():
+    spec = wl.MeshSpec(ndim=3, nb=(2, 1, 1), bs=(16, 16, 16))
+    U0 = wl.uniform_state(spec, 1.0, (0.0, 0.0, 0.0), 1.0)
+    U0[1, 4, 3, 3, 3] = -1.0          # negative total energy -> p < 0
+    from .gpu_helpers import gpu_batch_steps
+    with pytest.raises(B.OrchaError) as ei:
+        gpu_batch_steps([(spec, U0, None)], 1)
+    assert ei.value.status == B.ORCHA_ERR_NONFINITE

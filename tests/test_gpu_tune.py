@@ -27,7 +27,9 @@ def _cuda():
 
 @pytest.mark.parametrize("ndim,bs,task", [(3, (16, 16, 16), B.ORCHA_TASK_HYDRO_FP64),
                                           (3, (8, 8, 8), B.ORCHA_TASK_HYDRO_F32FLUX),
-                                          (2, (32, 16, 1), B.ORCHA_TASK_HYDRO_FP64)])
+                                          (2, (32, 16, 1), B.ORCHA_TASK_HYDRO_FP64),
+                                          (3, (16, 16, 16), B.ORCHA_TASK_HYDRO_FF),
+                                          (3, (16, 16, 16), B.ORCHA_TASK_HYDRO_RK2)])
 def test_autotune_picks_a_valid_tile_and_caches_it(tmp_path, ndim, bs, task):
     cache = str(tmp_path / "tiles.json")
     tx, ty, ms = B.orcha_autotune(ndim, bs, task, nblocks=64, cache_path=cache)
