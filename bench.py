@@ -81,6 +81,8 @@ def parse():
                              "sedov128_rk2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the oracle in the reference arm (0: all)")
     return ap.parse_args()
 
 
@@ -212,15 +214,16 @@ def run_reference(args):
     spec, packets, nt, task, desc = workload(args.workload)
     U0 = wl.sedov_state(spec)
     import oracle
-    threads = os.cpu_count() or 1
+    threads = args.cpu_threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     m = oracle.Mesh(**spec.oracle_kwargs())
     U = U0.copy()
+    step = oracle.step_rk2 if task == "rk2" else oracle.step
     for _ in range(args.warmup):
-        U, _, _ = oracle.step(m, U, oracle.dt(m, U))
+        U, _, _ = step(m, U, oracle.dt(m, U))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        U, _, _ = oracle.step(m, U, oracle.dt(m, U))
+        U, _, _ = step(m, U, oracle.dt(m, U))
     el = time.perf_counter() - t0
     value = spec.zones * args.steps / el
     sample = f"{args.steps} time steps (1 per bench step) of the full {spec.zones}-zone mesh, FP64"
