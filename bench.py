@@ -342,7 +342,7 @@ def main():
         achieved = flops * zones_per_launch / avg_launch_s / 1e12
         kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
         traffic = (profiled_traffic("persistent_kernel_fp64_sedov128.md", kname)
-                   if args.workload == "sedov128" else None)
+                   if args.workload == "sedov128" else None)        # RK2: a step is two launches; not recorded
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": kname, "per_launch": "one time step of all packets" + (
