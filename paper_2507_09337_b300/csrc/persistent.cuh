@@ -68,10 +68,10 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // Resident CTAs per SM requested from the register allocator (A/B-measured
 // on a B300): the FP64 variant, bound by the FP64 pipe, gains from 384
 // threads per SM (a small spill; +2 %); the FP32-flux variant runs best at
-// 512 threads per SM (128 registers) and loses from the spills of more. The
-// double-word variant has the FP64 variant's register and shared-memory
-// footprint (8-byte values) and takes its bound.
-template <class T, int NT> struct MinBlocks { static constexpr int value = (512 / NT) > 1 ? (512 / NT) : 1; };
+// 640 threads per SM (96 registers, a small spill: +5.6 % over 512; 768 and
+// more lose to the spills). The double-word variant has the FP64 variant's
+// register and shared-memory footprint (8-byte values) and takes its bound.
+template <class T, int NT> struct MinBlocks { static constexpr int value = (640 / NT) > 1 ? (640 / NT) : 1; };
 template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 

@@ -60,9 +60,11 @@ def test_batch_tiles_and_graph_replay(tile):
     assert np.array_equal(H, ref)
 
 
-def test_multi_mesh_batch_mixed_block_sizes():
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_RK2, B.ORCHA_TASK_HYDRO_FF])
+def test_multi_mesh_batch_mixed_block_sizes(task):
     """Meshes with 8^3, 16^3 and 32^3 blocks (different dt each) in one batch of
-    8x8 tiles: each result equals the mesh advanced alone."""
+    8x8 tiles: each result equals the mesh advanced alone (for RK2 each mesh's
+    two stages share the launches, and dt stays per mesh)."""
     probs = [
         (wl.MeshSpec(ndim=3, nb=(3, 2, 2), bs=(8, 8, 8)), 51),
         (wl.MeshSpec(ndim=3, nb=(2, 1, 1), bs=(16, 16, 16), periodic=(1, 1, 1)), 52),
@@ -76,8 +78,8 @@ def test_multi_mesh_batch_mixed_block_sizes():
         ids = rng.permutation(spec.nblocks).astype(np.int32)
         pk = np.array_split(ids, 2) if spec.nblocks > 1 else [ids]
         problems.append((spec, U0, pk))
-        alone.append(gpu_steps(spec, U0, 4)[0])
-    outs, errs = gpu_batch_steps(problems, 4, tile=(8, 8))
+        alone.append(gpu_steps(spec, U0, 4, task=task)[0])
+    outs, errs = gpu_batch_steps(problems, 4, tile=(8, 8), task=task)
     assert errs == [0, 0, 0]
     for G, A in zip(outs, alone):
         assert np.array_equal(G, A)
