@@ -224,9 +224,14 @@ ORCHA_API orcha_status orcha_dt_reduce(orcha_mesh* mesh, void* stream);
  *   if (init_dt) SIGNAL_SPEED on every packet, dt_reduce;
  *   repeat nsteps: GUARD_FILL on every packet; hydro_task on every packet;
  *                  dt_reduce; swap.
+ * hydro_task: HYDRO_FP64, HYDRO_F32FLUX, HYDRO_FF, or HYDRO_RK2, whose step
+ * is GUARD_FILL, RK2_STAGE1, swap, GUARD_FILL, RK2_STAGE2, dt_reduce, swap
+ * (the current buffer is the same before and after a step).
  * use_graph != 0 captures the nsteps-step sequence in a CUDA graph the first
  * time and replays it afterwards (the graph is cached on the mesh, keyed by
- * the packet set, task, step count and current buffer). */
+ * the packet set, task, step count and current buffer). Errors: INVALID
+ * (packets not covering the mesh, not a whole-step task, graph capture on
+ * the legacy default stream), CUDA. */
 ORCHA_API orcha_status orcha_mesh_advance(orcha_mesh* mesh, orcha_packet* const* packets, int32_t npackets,
                                 orcha_task hydro_task, int32_t nsteps, int32_t init_dt,
                                 int32_t use_graph, void* stream);
@@ -249,12 +254,15 @@ ORCHA_API orcha_status orcha_batch_create(orcha_packet* const* packets, int32_t 
                                           orcha_batch** out);
 ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
 
-/* nsteps steps of every mesh in the batch on `stream`. init_dt != 0 first
- * forms each mesh's dt from its current state (signal-speed task + dt
- * reduce); otherwise each mesh's dt_dev must already hold its time step.
- * use_graph != 0 captures the nsteps launches once per (task, nsteps) and
- * replays the graph (needs a non-default stream). After the call each
- * mesh's current buffer is the one its last step wrote. */
+/* nsteps steps of every mesh in the batch on `stream` (hydro_task as for
+ * orcha_mesh_advance; a HYDRO_RK2 step is two launches, one per stage).
+ * init_dt != 0 first forms each mesh's dt from its current state
+ * (signal-speed task + dt reduce); otherwise each mesh's dt_dev must already
+ * hold its time step. use_graph != 0 captures the nsteps steps' launches
+ * once per (task, nsteps) and replays the graph (needs a non-default
+ * stream). After the call each mesh's current buffer is the one its last
+ * step wrote. Errors: INVALID, UNSUPPORTED (the variant does not fit an SM),
+ * OOM, CUDA. */
 ORCHA_API orcha_status orcha_batch_advance(orcha_batch* batch, orcha_task hydro_task, int32_t nsteps,
                                            int32_t init_dt, int32_t use_graph, void* stream);
 
