@@ -224,6 +224,8 @@ ORCHA_API orcha_status orcha_dt_reduce(orcha_mesh* mesh, void* stream);
  *   if (init_dt) SIGNAL_SPEED on every packet, dt_reduce;
  *   repeat nsteps: GUARD_FILL on every packet; hydro_task on every packet;
  *                  dt_reduce; swap.
+ * For HYDRO_F32FLUX the first dt uses that task's FP32 signal-speed rule
+ * (as every later step's dt does); otherwise the FP64 SIGNAL_SPEED task.
  * hydro_task: HYDRO_FP64, HYDRO_F32FLUX, HYDRO_FF, or HYDRO_RK2, whose step
  * is GUARD_FILL, RK2_STAGE1, swap, GUARD_FILL, RK2_STAGE2, dt_reduce, swap
  * (the current buffer is the same before and after a step).

@@ -358,7 +358,8 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
     orcha_status s;
     if (init_dt) {
         // the packets cover every block: one launch over the whole mesh
-        ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], (cudaStream_t)stream),
+        ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], (cudaStream_t)stream,
+                                                  orcha::prec_of(task) == orcha::kF32),
                    "advance signal speed");
         if ((s = orcha_dt_reduce(m, stream))) return s;
     }
@@ -607,7 +608,8 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
     if (init_dt) {
         // one launch per mesh over all its blocks (the batch covers every block)
         for (auto* m : b->meshes) {
-            ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st),
+            ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st,
+                                                      orcha::prec_of(task) == orcha::kF32),
                        "batch signal speed");
             if ((s = orcha_dt_reduce(m, stream))) return s;
         }

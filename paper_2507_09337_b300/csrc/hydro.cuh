@@ -226,6 +226,29 @@ __device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, 
     return (unsigned long long)bits(s);   // s >= 0 or NaN
 }
 
+// The FP32-flux variant's signal speed (new_state_speed<float>: FP32, rounded
+// up by 1 + 2^-18, FP64 where the FP32 pressure is not positive) over the
+// interior cells of block `blk` handled by this thread; the first time step
+// of an FP32-flux run comes from the same rule as every later one.
+__device__ __forceinline__ unsigned long long block_signal_speed_f32(const MeshDev& m, int blk,
+                                                                     const double* __restrict__ U) {
+    const double* Ub = U + (long long)blk * m.blk_stride;
+    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    unsigned long long smaxb = 0ull;
+    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]),
+                  k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+        const int kk = (m.ndim == 3) ? k + kGuard : 0;
+        const long long po = ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+        rd Uc[5];
+        for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
+        const unsigned long long b =
+            (m.ndim == 3) ? new_state_speed<float, 3>(m, Uc) : new_state_speed<float, 2>(m, Uc);
+        smaxb = umax64(smaxb, b);
+    }
+    return smaxb;
+}
+
 // ---------------------------------------------------------------- the kernel
 
 template <int NDIM, int TX, int TY>

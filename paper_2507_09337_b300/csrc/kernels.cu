@@ -109,11 +109,13 @@ __global__ void signal_speed_kernel(const MeshDev m, const int* __restrict__ blk
     cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
 }
 
-// Every block of the mesh, one CTA per block (no block-id list).
+// Every block of the mesh, one CTA per block (no block-id list); F32: the
+// FP32-flux variant's signal-speed rule.
+template <bool F32>
 __global__ void signal_speed_all_kernel(const MeshDev m, const double* __restrict__ U) {
     __shared__ unsigned long long red[32];
     const int blk = blockIdx.x;
-    const unsigned long long b = block_signal_speed(m, blk, U);
+    const unsigned long long b = F32 ? block_signal_speed_f32(m, blk, U) : block_signal_speed(m, blk, U);
     cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
 }
 
@@ -569,8 +571,9 @@ cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st) {
-    signal_speed_all_kernel<<<(unsigned)nblk, 256, 0, st>>>(m, U);
+cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st, bool f32) {
+    if (f32) signal_speed_all_kernel<true><<<(unsigned)nblk, 256, 0, st>>>(m, U);
+    else signal_speed_all_kernel<false><<<(unsigned)nblk, 256, 0, st>>>(m, U);
     return cudaGetLastError();
 }
 

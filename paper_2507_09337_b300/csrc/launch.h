@@ -62,7 +62,9 @@ cudaError_t launch_unpack_ids(const MeshDev& m, const int* ids, int n, const dou
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
 // Signal speed of every block 0..nblk-1 (one CTA per block, no id list).
-cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st);
+// f32: the FP32-flux variant's signal-speed rule (its first dt), else FP64.
+cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st,
+                                   bool f32 = false);
 // Two conserved states of a two-region initial state (serving recipes).
 struct RegionStates {
     double in[5], out[5];

@@ -231,7 +231,8 @@ bool orcha_server::admit(Req* r) {
         SRV_CUDA(orcha::launch_region_init(r->m, r->state[0], r->d.init_kind, reg, rs, copy), "admit recipe");
     }
     SRV_CUDA(cudaMemsetAsync(tail, 0, tail_bytes, copy), "admit clear");
-    SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy), "admit signal speed");
+    SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy, r->prec == orcha::kF32),
+             "admit signal speed");
     SRV_CUDA(orcha::launch_dt_reduce(r->m, (int)r->nblk, r->dt, copy), "admit dt");
     SRV_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "admit event");
     SRV_CUDA(cudaEventRecord(r->ev, copy), "admit record");
