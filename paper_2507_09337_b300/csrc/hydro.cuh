@@ -168,16 +168,18 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
 // Largest signal speed sum_d (|u_d| + c) / dx_d over the interior cells of
 // block `blk` of the padded state U handled by this thread (stride
 // blockDim.x), as the bits of a non-negative double; flags non-physical cells.
+// (chunk, nchunks): this CTA takes cells chunk * blockDim.x + t, stepping
+// nchunks * blockDim.x.
 __device__ __forceinline__ unsigned long long block_signal_speed(const MeshDev& m, int blk,
-                                                                 const double* __restrict__ U) {
+                                                                 const double* __restrict__ U, int chunk = 0,
+                                                                 int nchunks = 1) {
     const double* Ub = U + (long long)blk * m.blk_stride;
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
     unsigned long long smaxb = 0ull;
-    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]),
-                  k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+    for (int c = chunk * blockDim.x + threadIdx.x; c < ncell; c += nchunks * blockDim.x) {
+        const int i = c % m.bs[0], r0 = c / m.bs[0], j = r0 % m.bs[1], k = r0 / m.bs[1];
         const int kk = (m.ndim == 3) ? k + kGuard : 0;
-        const long long po = ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+        const int po = (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
         rd Uc[5], W[5], r;
         for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
         if (m.ndim == 3) prim_from_cons<rd, 3>(Uc, W, r, rd(m.gm1));
@@ -231,15 +233,15 @@ __device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, 
 // interior cells of block `blk` handled by this thread; the first time step
 // of an FP32-flux run comes from the same rule as every later one.
 __device__ __forceinline__ unsigned long long block_signal_speed_f32(const MeshDev& m, int blk,
-                                                                     const double* __restrict__ U) {
+                                                                     const double* __restrict__ U, int chunk = 0,
+                                                                     int nchunks = 1) {
     const double* Ub = U + (long long)blk * m.blk_stride;
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
     unsigned long long smaxb = 0ull;
-    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]),
-                  k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+    for (int c = chunk * blockDim.x + threadIdx.x; c < ncell; c += nchunks * blockDim.x) {
+        const int i = c % m.bs[0], r0 = c / m.bs[0], j = r0 % m.bs[1], k = r0 / m.bs[1];
         const int kk = (m.ndim == 3) ? k + kGuard : 0;
-        const long long po = ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+        const int po = (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
         rd Uc[5];
         for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
         const unsigned long long b =

@@ -23,13 +23,13 @@ __device__ __forceinline__ int map_axis(int gi, int n, int periodic) {
 }
 
 __global__ void guard_fill_kernel(const MeshDev m, const int* __restrict__ blk_ids, double* __restrict__ U) {
-    const long long npad = m.var_stride;
+    const int npad = (int)m.var_stride;                  // a padded block has at most 36^3 cells
     const int pb = blockIdx.y;
     const int blk = blk_ids[pb];
     const int b[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < npad;
-         c += (long long)gridDim.x * blockDim.x) {
-        int loc[3] = {(int)(c % m.pad[0]), (int)((c / m.pad[0]) % m.pad[1]), (int)(c / ((long long)m.pad[0] * m.pad[1]))};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < npad; c += gridDim.x * blockDim.x) {
+        const int r = c / m.pad[0];
+        int loc[3] = {c % m.pad[0], r % m.pad[1], r / m.pad[1]};
         bool guard = false;
         int src_blk[3], src_loc[3];
         for (int d = 0; d < 3; ++d) {
@@ -51,54 +51,53 @@ __global__ void guard_fill_kernel(const MeshDev m, const int* __restrict__ blk_i
 }
 
 // ---------------------------------------------------------------- pack / unpack
-// Interior array [block][var][k][j][i] <-> padded state interior.
-__device__ __forceinline__ long long padded_offset(const MeshDev& m, long long e, long long ncell) {
-    const long long bv = e / ncell;               // block * nvar + var
-    const long long c = e % ncell;
-    const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
+// Interior array [block][var][k][j][i] <-> padded state interior. One CTA per
+// (block, var) plane; in-block cell indices are 32-bit (a block has at most
+// 32^3 cells), so no 64-bit division runs per cell.
+__device__ __forceinline__ int cell_offset(const MeshDev& m, int c) {
+    const int i = c % m.bs[0], r = c / m.bs[0];
+    const int j = r % m.bs[1], k = r / m.bs[1];
     const int kk = (m.ndim == 3) ? k + kGuard : 0;
-    return bv * m.var_stride + ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+    return (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
 }
 
+// plane p = block * nvar + var of the packed array; dst block `blk`
 __global__ void pack_kernel(const MeshDev m, const double* __restrict__ interior, double* __restrict__ U) {
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * ncell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        U[padded_offset(m, e, ncell)] = interior[e];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const long long p = blockIdx.x;
+    const double* src = interior + p * ncell;
+    double* dst = U + p * m.var_stride;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) dst[cell_offset(m, c)] = src[c];
 }
 
 __global__ void unpack_kernel(const MeshDev m, const double* __restrict__ U, double* __restrict__ interior) {
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * ncell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        interior[e] = U[padded_offset(m, e, ncell)];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const long long p = blockIdx.x;
+    const double* src = U + p * m.var_stride;
+    double* dst = interior + p * ncell;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) dst[c] = src[cell_offset(m, c)];
 }
 
 // The same for the blocks of one packet: `interior` holds them in packet
-// order, [packet position][var][k][j][i].
-__device__ __forceinline__ long long packet_offset(const MeshDev& m, const int* ids, long long e, long long ncell) {
-    const long long per_blk = (long long)m.nvar * ncell;
-    return padded_offset(m, (long long)ids[e / per_blk] * per_blk + e % per_blk, ncell);
-}
-
+// order, [packet position][var][k][j][i]; plane p = position * nvar + var.
 __global__ void pack_ids_kernel(const MeshDev m, const int* __restrict__ ids, int n,
                                 const double* __restrict__ interior, double* __restrict__ U) {
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    const long long total = (long long)n * m.nvar * ncell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        U[packet_offset(m, ids, e, ncell)] = interior[e];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const long long p = blockIdx.x;
+    const long long pos = p / m.nvar, v = p % m.nvar;
+    const double* src = interior + p * ncell;
+    double* dst = U + (long long)ids[pos] * m.blk_stride + v * m.var_stride;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) dst[cell_offset(m, c)] = src[c];
 }
 
 __global__ void unpack_ids_kernel(const MeshDev m, const int* __restrict__ ids, int n, const double* __restrict__ U,
                                   double* __restrict__ interior) {
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    const long long total = (long long)n * m.nvar * ncell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        interior[e] = U[packet_offset(m, ids, e, ncell)];
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const long long p = blockIdx.x;
+    const long long pos = p / m.nvar, v = p % m.nvar;
+    const double* src = U + (long long)ids[pos] * m.blk_stride + v * m.var_stride;
+    double* dst = interior + p * ncell;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) dst[c] = src[cell_offset(m, c)];
 }
 
 // ---------------------------------------------------------------- signal speed of the current state
@@ -115,8 +114,9 @@ template <bool F32>
 __global__ void signal_speed_all_kernel(const MeshDev m, const double* __restrict__ U) {
     __shared__ unsigned long long red[32];
     const int blk = blockIdx.x;
-    const unsigned long long b = F32 ? block_signal_speed_f32(m, blk, U) : block_signal_speed(m, blk, U);
-    cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);
+    const unsigned long long b = F32 ? block_signal_speed_f32(m, blk, U, blockIdx.y, gridDim.y)
+                                     : block_signal_speed(m, blk, U, blockIdx.y, gridDim.y);
+    cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);     // max: any chunk order
 }
 
 // ---------------------------------------------------------------- dt reduction
@@ -180,13 +180,12 @@ cudaError_t launch_synthetic_state(const MeshDev& m, double* U, cudaStream_t st)
 // region test is integer arithmetic and the states are given, so the values
 // are exact and match any other implementation of the same rule.
 __global__ void region_init_kernel(const MeshDev m, double* __restrict__ U, int kind, int4 reg, RegionStates rs) {
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * ncell;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long blk = e / ncell, c = e % ncell;
-        const int l[3] = {(int)(c % m.bs[0]), (int)((c / m.bs[0]) % m.bs[1]), (int)(c / ((long long)m.bs[0] * m.bs[1]))};
-        const int b[3] = {(int)(blk % m.nb[0]), (int)((blk / m.nb[0]) % m.nb[1]), (int)(blk / ((long long)m.nb[0] * m.nb[1]))};
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const int blk = blockIdx.x;
+    const int b[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
+    double* Ub = U + (long long)blk * m.blk_stride;
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncell; c += gridDim.y * blockDim.x) {
+        const int l[3] = {c % m.bs[0], (c / m.bs[0]) % m.bs[1], c / (m.bs[0] * m.bs[1])};
         long long g[3];
         for (int d = 0; d < 3; ++d) g[d] = (long long)b[d] * m.bs[d] + l[d];
         bool in;
@@ -201,9 +200,8 @@ __global__ void region_init_kernel(const MeshDev m, double* __restrict__ U, int 
         } else {
             in = g[reg.x] < reg.y;
         }
-        const int kk = (m.ndim == 3) ? l[2] + kGuard : 0;
-        const long long po = blk * m.blk_stride + ((long long)kk * m.pad[1] + (l[1] + kGuard)) * m.pad[0] + (l[0] + kGuard);
-        for (int v = 0; v < m.nvar; ++v) U[po + v * m.var_stride] = in ? rs.in[v] : rs.out[v];
+        const int po = cell_offset(m, c);
+        for (int v = 0; v < m.nvar; ++v) Ub[po + v * m.var_stride] = in ? rs.in[v] : rs.out[v];
     }
 }
 
@@ -214,14 +212,12 @@ __global__ void region_init_kernel(const MeshDev m, double* __restrict__ U, int 
 __global__ void block_totals_kernel(const MeshDev m, const double* __restrict__ U, double* __restrict__ partial) {
     __shared__ double red[256];
     const int blk = blockIdx.x;
-    const long long ncell = (long long)m.bs[0] * m.bs[1] * m.bs[2];
-    for (int v = 0; v < m.nvar; ++v) {
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    {
+        const int v = blockIdx.y;                    // one CTA per (block, variable)
         double acc = 0.0;
-        for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-            const int i = (int)(c % m.bs[0]), j = (int)((c / m.bs[0]) % m.bs[1]), k = (int)(c / ((long long)m.bs[0] * m.bs[1]));
-            const int kk = (m.ndim == 3) ? k + kGuard : 0;
-            acc += U[(long long)blk * m.blk_stride + v * m.var_stride + ((long long)kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard)];
-        }
+        const double* Uv = U + (long long)blk * m.blk_stride + v * m.var_stride;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) acc += Uv[cell_offset(m, c)];
         red[threadIdx.x] = acc;
         __syncthreads();
         for (int o = 128; o > 0; o >>= 1) {
@@ -250,13 +246,20 @@ __global__ void sum_partials_kernel(const MeshDev m, int nblk, const double* __r
     }
 }
 
+// CTAs per block for the per-cell utility kernels: one per 4096 cells.
+static unsigned cell_chunks(const MeshDev& m) {
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    return (unsigned)((ncell + 4095) / 4096);
+}
+
 cudaError_t launch_region_init(const MeshDev& m, double* U, int kind, int4 reg, const RegionStates& rs, cudaStream_t st) {
-    region_init_kernel<<<148 * 4, 256, 0, st>>>(m, U, kind, reg, rs);
+    region_init_kernel<<<dim3((unsigned)(m.nb[0] * m.nb[1] * m.nb[2]), cell_chunks(m)), 256, 0, st>>>(m, U, kind, reg,
+                                                                                                      rs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_totals(const MeshDev& m, int nblk, const double* U, double* partial, double* out, cudaStream_t st) {
-    block_totals_kernel<<<(unsigned)nblk, 256, 0, st>>>(m, U, partial);
+    block_totals_kernel<<<dim3((unsigned)nblk, (unsigned)m.nvar), 256, 0, st>>>(m, U, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sum_partials_kernel<<<1, 256, 0, st>>>(m, nblk, partial, out);
@@ -530,39 +533,27 @@ cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U
     return cudaGetLastError();
 }
 
-static unsigned copy_grid(const MeshDev& m, int threads) {
-    const long long total = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar * m.bs[0] * m.bs[1] * m.bs[2];
-    long long blocks = (total + threads - 1) / threads;
-    if (blocks > 148 * 32) blocks = 148 * 32;
-    return (unsigned)blocks;
-}
-
 cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cudaStream_t st) {
-    pack_kernel<<<copy_grid(m, 256), 256, 0, st>>>(m, interior, U);
+    const long long planes = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar;
+    pack_kernel<<<(unsigned)planes, 256, 0, st>>>(m, interior, U);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const MeshDev& m, const double* U, double* interior, cudaStream_t st) {
-    unpack_kernel<<<copy_grid(m, 256), 256, 0, st>>>(m, U, interior);
+    const long long planes = (long long)m.nb[0] * m.nb[1] * m.nb[2] * m.nvar;
+    unpack_kernel<<<(unsigned)planes, 256, 0, st>>>(m, U, interior);
     return cudaGetLastError();
-}
-
-static unsigned packet_grid(const MeshDev& m, int n, int threads) {
-    const long long total = (long long)n * m.nvar * m.bs[0] * m.bs[1] * m.bs[2];
-    long long blocks = (total + threads - 1) / threads;
-    if (blocks > 148 * 32) blocks = 148 * 32;
-    return (unsigned)(blocks < 1 ? 1 : blocks);
 }
 
 cudaError_t launch_pack_ids(const MeshDev& m, const int* ids, int n, const double* interior, double* U,
                             cudaStream_t st) {
-    pack_ids_kernel<<<packet_grid(m, n, 256), 256, 0, st>>>(m, ids, n, interior, U);
+    pack_ids_kernel<<<(unsigned)((long long)n * m.nvar), 256, 0, st>>>(m, ids, n, interior, U);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_ids(const MeshDev& m, const int* ids, int n, const double* U, double* interior,
                               cudaStream_t st) {
-    unpack_ids_kernel<<<packet_grid(m, n, 256), 256, 0, st>>>(m, ids, n, U, interior);
+    unpack_ids_kernel<<<(unsigned)((long long)n * m.nvar), 256, 0, st>>>(m, ids, n, U, interior);
     return cudaGetLastError();
 }
 
@@ -572,8 +563,9 @@ cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const d
 }
 
 cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st, bool f32) {
-    if (f32) signal_speed_all_kernel<true><<<(unsigned)nblk, 256, 0, st>>>(m, U);
-    else signal_speed_all_kernel<false><<<(unsigned)nblk, 256, 0, st>>>(m, U);
+    const dim3 grid((unsigned)nblk, cell_chunks(m));
+    if (f32) signal_speed_all_kernel<true><<<grid, 256, 0, st>>>(m, U);
+    else signal_speed_all_kernel<false><<<grid, 256, 0, st>>>(m, U);
     return cudaGetLastError();
 }
 
