@@ -179,3 +179,32 @@ def test_nonphysical_request_reports_device_error():
         assert srv.wait(t2).status == 0
     finally:
         srv.close()
+
+
+def test_2d_requests_in_flight_with_3d_ones(oracle_mod):
+    """2D requests (their own launch groups) served together with 3D ones:
+    each 2D result matches the oracle and the packet path, and the 3D results
+    equal those served alone."""
+    from .gpu_helpers import gpu_steps
+    g = 1.4
+    reqs2d = []
+    for nb, bs, axis in [((4, 2, 1), (16, 16, 1), 0), ((3, 5, 1), (8, 8, 1), 1)]:
+        spec = wl.MeshSpec(ndim=2, nb=nb, bs=bs, hi=(1.0, nb[1] * bs[1] / (nb[0] * bs[0]), 1.0))
+        n_ax = nb[axis] * bs[axis]
+        u_in = tuple(wl._cons(g, 1.0, 1.0, 2))         # (rho, m_x, m_y, E), padded to five
+        u_out = tuple(wl._cons(g, 0.125, 0.1, 2))
+        reqs2d.append(dict(spec=spec, kind=B.ORCHA_INIT_HALF_SPACE, region=(axis, n_ax // 2, 0, 0),
+                           u_in=u_in, u_out=u_out, nsteps=3))
+    reqs3d = _requests(3, 21, max_blocks=6, sizes=(8, 16), nsteps=3)
+    alone3d = [_serve([r])[0][0] for r in reqs3d]
+    mixed, stats, _ = _serve(reqs2d + reqs3d)
+    assert all(s.status == 0 for s in stats)
+    for r, G in zip(reqs2d, mixed[:2]):
+        spec = r["spec"]
+        U0 = wl.region_state(spec, r["kind"], r["region"], r["u_in"], r["u_out"])
+        O, _ = oracle_steps(oracle_mod, spec, U0, 3)
+        assert rule12_error(G, O, spec.nvar) <= 1e-12
+        P, _, _ = gpu_steps(spec, U0, 3)
+        assert np.array_equal(G, P)
+    for A, M in zip(alone3d, mixed[2:]):
+        assert np.array_equal(A, M)
