@@ -366,46 +366,55 @@ def main():
     hbm_eff = BYTES_PER_ZONE_3D * value / world / 1e9
 
     # end to end through the public API with host buffers: every step copies its
-    # input from pinned host memory and its result back. Two meshes on two
-    # streams alternate, so one step's copies overlap the other's compute (the
+    # input from pinned host memory and its result back. Three meshes on three
+    # streams take turns, so while one computes, another's result copy (D2H)
+    # and a third's input copy (H2D) run on the two copy engines at once (the
     # way a caller streams independent problems through the library).
+    NLANES = 3
     U0_pin = torch.from_numpy(U0_host).pin_memory()
-    out_pin = [torch.empty(U0_host.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    out_pin = [torch.empty(U0_host.shape, dtype=torch.float64).pin_memory() for _ in range(NLANES)]
     bytes_io = U0_host.nbytes
-    mesh2 = B.Mesh(spec, device=f"cuda:{local}", packets=packets)
-    batch2 = B.orcha_batch_create(mesh2.packets, tile[0], tile[1])
-    stream2 = torch.cuda.Stream(dev)
-    stream2.wait_stream(torch.cuda.current_stream(dev))
-    lanes = [(h, batch, stream, out_pin[0]), (mesh2.handle, batch2, stream2, out_pin[1])]
+    lanes = [(h, batch, stream, out_pin[0])]
+    extra = []
+    for k in range(1, NLANES):
+        mk = B.Mesh(spec, device=f"cuda:{local}", packets=packets)
+        bk = B.orcha_batch_create(mk.packets, tile[0], tile[1])
+        sk = torch.cuda.Stream(dev)
+        sk.wait_stream(torch.cuda.current_stream(dev))
+        extra.append((mk, bk))
+        lanes.append((mk.handle, bk, sk, out_pin[k]))
 
     def e2e_step(k):
-        hk, bk, sk, ok = lanes[k % 2]
+        hk, bk, sk, ok = lanes[k % NLANES]
         B.orcha_mesh_load(hk, U0_pin.data_ptr(), True, sk)
         B.orcha_batch_advance(bk, task, nt, True, True, sk)
         B.orcha_mesh_store(hk, ok.data_ptr(), True, sk)
 
-    for k in range(2):
+    for k in range(NLANES):
         e2e_step(k)
-    stream.synchronize()
-    stream2.synchronize()
+    for lane in lanes:
+        lane[2].synchronize()
     if world > 1:
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    mid = torch.cuda.Event()
     e0.record(stream)
-    stream2.wait_event(e0)
+    for lane in lanes[1:]:
+        lane[2].wait_event(e0)
     for k in range(args.steps):
         e2e_step(k)
-    mid.record(stream2)
-    stream.wait_event(mid)
+    for lane in lanes[1:]:
+        done = torch.cuda.Event()
+        done.record(lane[2])
+        stream.wait_event(done)
     e1.record(stream)
     stream.synchronize()
     e2e_value = job_rate(spec.zones * nt * args.steps, world, max_over_ranks(e0.elapsed_time(e1), dev))
-    assert mesh2.poll(stream2) == 0
+    for (mk, _), lane in zip(extra, lanes[1:]):
+        assert mk.poll(lane[2]) == 0
     assert mesh.poll(stream) == 0
     # the e2e runs and the device-resident run computed the same state
-    assert torch.equal(out_pin[0], out_dev.cpu()) and torch.equal(out_pin[1], out_dev.cpu())
+    assert all(torch.equal(o, out_dev.cpu()) for o in out_pin)
 
     line = {
         "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": world,
@@ -422,8 +431,8 @@ def main():
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io, "api": "orcha_mesh_load(host) + orcha_batch_advance(graph) + "
-                                                         "orcha_mesh_store(host); two meshes on two streams "
-                                                         "alternate so copies overlap compute"},
+                                                         "orcha_mesh_store(host); three meshes on three streams "
+                                                         "take turns so copies overlap compute"},
         "gpu_launches": launches_per_step * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -431,8 +440,9 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{n} time steps of the full {spec.zones}-zone mesh in {el:.1f} s"}
     B.orcha_batch_destroy(batch)
-    B.orcha_batch_destroy(batch2)
-    mesh2.close()
+    for mk, bk in extra:
+        B.orcha_batch_destroy(bk)
+        mk.close()
     mesh.close()
     if rank == 0:
         print(json.dumps(line))
