@@ -277,7 +277,6 @@ template <> struct P<float> {
 #include "dword.cuh"
 namespace orcha {
 template <> __device__ __forceinline__ dw as<dw, dw>(dw x) { return x; }
-template <> __device__ __forceinline__ dw2 as<dw2, dw2>(dw2 x) { return x; }
 template <> struct P<dw> {
     using store = dw;
     // binary64 -> double-word: hi = x rounded to binary32, lo = (x - hi)
@@ -307,13 +306,6 @@ template <> struct P<dw> {
     static __device__ __forceinline__ dw half(dw x) { return {__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)}; }
     static __device__ __forceinline__ dw zero() { return dw{0.0f, 0.0f}; }
     static __device__ __forceinline__ double to_double(dw x) { return __dadd_rn(to_f64(x.hi), to_f64(x.lo)); }
-};
-
-// Two double-words per lane pair: only what the shared point functions use.
-template <> struct P<dw2> {
-    static __device__ __forceinline__ dw2 half(dw2 x) {
-        return {dwx::mul2(dwx::splat2(0.5f), x.hi), dwx::mul2(dwx::splat2(0.5f), x.lo)};
-    }
 };
 
 // ---------------------------------------------------------------- float-float (error-free transformations)

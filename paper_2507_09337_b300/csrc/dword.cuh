@@ -108,71 +108,4 @@ __device__ __forceinline__ dw dw_rsqrt(dw y) {
 // Totally ordered comparison of normalised double-words.
 __device__ __forceinline__ bool dw_lt(dw a, dw b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
-// ---------------------------------------------------------------- two double-words per instruction
-// dw2 carries two independent double-words in the x and y lanes of float2
-// pairs. Each operation is the dw operation above applied to both lanes with
-// the packed FP32x2 instructions (add / mul / fma .f32x2, round to nearest
-// even per lane, never contracted), so every lane gets the same bits as the
-// scalar operation while one instruction issue does the work of two.
-struct dw2 {
-    float2 hi, lo;
-};
-
-namespace dwx {
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
-}  // namespace dwx
-
-__device__ __forceinline__ dw2 pack2(dw a, dw b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
-__device__ __forceinline__ dw lane_x(dw2 a) { return {a.hi.x, a.lo.x}; }
-__device__ __forceinline__ dw lane_y(dw2 a) { return {a.hi.y, a.lo.y}; }
-
-__device__ __forceinline__ dw2 operator+(dw2 x, dw2 y) {
-    using namespace dwx;
-    const float2 sh = add2(x.hi, y.hi);                   // 2Sum of the high parts
-    const float2 ap = sub2(sh, y.hi);
-    const float2 bp = sub2(sh, ap);
-    const float2 sl = add2(sub2(x.hi, ap), sub2(y.hi, bp));
-    const float2 w = add2(sl, add2(x.lo, y.lo));
-    const float2 zh = add2(sh, w);                        // Fast2Sum
-    return {zh, sub2(w, sub2(zh, sh))};
-}
-__device__ __forceinline__ dw2 operator-(dw2 x) { return {dwx::neg2(x.hi), dwx::neg2(x.lo)}; }
-__device__ __forceinline__ dw2 operator-(dw2 x, dw2 y) { return x + (-y); }
-__device__ __forceinline__ dw2 operator*(dw2 x, dw2 y) {
-    using namespace dwx;
-    const float2 ch = mul2(x.hi, y.hi);
-    const float2 cl1 = fma2(x.hi, y.hi, neg2(ch));
-    const float2 cl2 = fma2(x.lo, y.hi, mul2(x.hi, y.lo));
-    return {ch, add2(cl1, cl2)};
-}
-__device__ __forceinline__ dw2 dw2_rsqrt(dw2 y) {
-    using namespace dwx;
-    const float2 r0 = make_float2(rsqrtf(y.hi.x), rsqrtf(y.hi.y));
-    const float2 e0 = fma2(neg2(mul2(y.hi, r0)), r0, splat2(1.0f));
-    const float2 r1 = fma2(mul2(splat2(0.5f), r0), e0, r0);
-    const float2 qh = mul2(r1, r1);
-    const float2 ql = fma2(r1, r1, neg2(qh));
-    float2 e = fma2(neg2(y.hi), qh, splat2(1.0f));
-    e = fma2(neg2(y.hi), ql, e);
-    e = fma2(neg2(y.lo), qh, e);
-    const float2 h = mul2(splat2(0.5f), e);
-    const float2 t = fma2(mul2(splat2(0.75f), e), h, h);
-    const float2 p = mul2(r1, t);
-    const float2 zh = add2(r1, p);
-    return {zh, sub2(p, sub2(zh, r1))};
-}
-// x * rsqrt(x * rho) per lane, 0 where x <= 0 (the other lane's value is
-// kept; a lane with x <= 0 computes a discarded NaN).
-__device__ __forceinline__ dw2 dw2_sound(dw2 x, dw2 rho) {
-    dw2 c = x * dw2_rsqrt(x * rho);
-    if (!(x.hi.x > 0.0f)) { c.hi.x = 0.0f; c.lo.x = 0.0f; }
-    if (!(x.hi.y > 0.0f)) { c.hi.y = 0.0f; c.lo.y = 0.0f; }
-    return c;
-}
-
 }  // namespace orcha

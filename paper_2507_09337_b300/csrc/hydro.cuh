@@ -127,38 +127,6 @@ __device__ __forceinline__ void cons_flux(const T* Wt, T* Ut, T* Ft, T igm1t) {
 template <class T, int NDIM, bool ZNORMAL>
 __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     constexpr int NV = NDIM + 2;
-    if constexpr (std::is_same<T, dw>::value) {
-        // Double-words: the left and right states ride in the two lanes of
-        // packed pairs (sound speeds, wave speeds, conserved states, fluxes),
-        // and the combination is the same HLL flux written as
-        // (S_R (F_L - S_L U_L) - S_L (F_R - S_R U_R)) / (S_R - S_L), whose
-        // first two steps are again one lane per side.
-        dw2 W[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) W[v] = pack2(L[v], R[v]);
-        const dw2 c = dw2_sound(pack2(g, g) * W[NV - 1], W[0]);
-        const dw2 lo = W[1] - c, hi = W[1] + c;
-        const dw SL = dw_lt(lane_x(lo), lane_y(lo)) ? lane_x(lo) : lane_y(lo);
-        const dw SR = dw_lt(lane_y(hi), lane_x(hi)) ? lane_x(hi) : lane_y(hi);
-        dw2 U2[NV], F2[NV];
-        cons_flux<dw2, dw2, NDIM, ZNORMAL>(W, U2, F2, pack2(igm1, igm1));
-        if (P<dw>::ge0(SL)) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] = lane_x(F2[v]);
-        } else if (P<dw>::le0(SR)) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] = lane_y(F2[v]);
-        } else {
-            const dw inv = dw_rcp(SR - SL);
-            const dw2 s_lr = pack2(SL, SR), s_rl = pack2(SR, SL);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const dw2 h = s_rl * (F2[v] - s_lr * U2[v]);      // (S_R G_L, S_L G_R)
-                F[v] = (lane_x(h) - lane_y(h)) * inv;
-            }
-        }
-        return;
-    }
     using AS = Arith<T, 32>;     // wave speeds
     using AC = Arith<T, 16>;     // combination
     const AS gs = as<AS>(g);
