@@ -525,12 +525,19 @@ bool hydro_tile_supported(int ndim, int tx, int ty) {
     return false;
 }
 
+// One grid row per packet block; a packet of more blocks than a grid has
+// rows (65,535) is filled by consecutive launches over slices of its ids.
 cudaError_t launch_guard_fill(const MeshDev& m, const int* ids, int n, double* U, cudaStream_t st) {
-    const int threads = 256;
+    const int threads = 256, max_rows = 65535;
     const long long npad = m.var_stride;
     const unsigned gx = (unsigned)((npad + threads - 1) / threads);
-    guard_fill_kernel<<<dim3(gx, (unsigned)n), threads, 0, st>>>(m, ids, U);
-    return cudaGetLastError();
+    for (int off = 0; off < n; off += max_rows) {
+        const int rows = n - off < max_rows ? n - off : max_rows;
+        guard_fill_kernel<<<dim3(gx, (unsigned)rows), threads, 0, st>>>(m, ids + off, U);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pack(const MeshDev& m, const double* interior, double* U, cudaStream_t st) {

@@ -36,15 +36,16 @@ def _smooth_state(spec):
     import torch
     dev = torch.device("cuda")
     nbx, nby, nbz = spec.nb
+    bs = spec.bs
     b = torch.arange(spec.nblocks, device=dev, dtype=torch.int64)
-    i = torch.arange(BS[0], device=dev, dtype=torch.float64)
 
-    def coord(bidx, n_cells, shape):
-        return ((bidx.to(torch.float64)[:, None] * BS[0] + i[None, :] + 0.5) / n_cells).reshape(shape)
+    def coord(bidx, a, shape):
+        i = torch.arange(bs[a], device=dev, dtype=torch.float64)
+        return ((bidx.to(torch.float64)[:, None] * bs[a] + i[None, :] + 0.5) / (spec.nb[a] * bs[a])).reshape(shape)
 
-    x = coord(b % nbx, nbx * BS[0], (-1, 1, 1, BS[0]))
-    y = coord((b // nbx) % nby, nby * BS[1], (-1, 1, BS[1], 1))
-    z = coord(b // (nbx * nby), nbz * BS[2], (-1, BS[2], 1, 1))
+    x = coord(b % nbx, 0, (-1, 1, 1, bs[0]))
+    y = coord((b // nbx) % nby, 1, (-1, 1, bs[1], 1))
+    z = coord(b // (nbx * nby), 2, (-1, bs[2], 1, 1))
     tp = 2.0 * math.pi
     rho = 1.0 + 0.2 * torch.sin(tp * x) * torch.sin(tp * y)
     u = 0.3 * torch.sin(tp * y) + 0.0 * z
@@ -122,3 +123,34 @@ def test_batch_equals_packet_path_and_conserves():
     scale[1:4] = torch.maximum(scale[1:4], U0[:, 0].sum())
     assert bool(torch.all((s1 - s0).abs() <= 1e-13 * scale)), ((s1 - s0) / scale).tolist()
     assert not torch.equal(A, U0)
+
+
+def test_one_packet_of_65536_blocks():
+    """A packet of more blocks than one launch has grid rows (65,535): the
+    packet path fills its guards over several launches and matches the
+    persistent batch bit for bit (8^3 blocks, 64 x 32 x 32 of them)."""
+    import torch
+    spec = wl.MeshSpec(ndim=3, nb=(64, 32, 32), bs=(8, 8, 8), periodic=(1, 1, 1))
+    U0 = _smooth_state(spec)
+    outs = []
+    for path in ("batch", "packets"):
+        mesh = B.Mesh(spec)                  # one packet of every block
+        try:
+            assert len(mesh.packets) == 1 and spec.nblocks == 65536
+            mesh.load(U0)
+            if path == "batch":
+                batch = B.orcha_batch_create(mesh.packets)
+                try:
+                    B.orcha_batch_advance(batch, B.ORCHA_TASK_HYDRO_FP64, 2, True, False)
+                finally:
+                    B.orcha_batch_destroy(batch)
+            else:
+                mesh.advance(2, B.ORCHA_TASK_HYDRO_FP64)
+            assert mesh.poll() == 0
+            out = torch.empty_like(U0)
+            mesh.store(out)
+            torch.cuda.synchronize()
+            outs.append(out)
+        finally:
+            mesh.close()
+    assert torch.equal(outs[0], outs[1]) and not torch.equal(outs[0], U0)
