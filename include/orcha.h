@@ -136,8 +136,9 @@ typedef struct orcha_mesh_desc {
     double* state_dev[2];/* two caller-owned device buffers of orcha_state_elems() doubles each,
                             layout [block][var][k][j][i] over the padded block
                             (bs + 4 cells per active axis, i fastest), vars
-                            (rho, m_x, m_y[, m_z], E); 8-byte aligned */
-    double* dt_dev;      /* caller-owned device double: the current time step */
+                            (rho, m_x, m_y[, m_z], E); 16-byte aligned (the
+                            kernels load pairs of x-neighbours as one vector) */
+    double* dt_dev;      /* caller-owned device double: the current time step (8-byte aligned) */
 } orcha_mesh_desc;
 
 typedef struct orcha_mesh orcha_mesh;     /* opaque */

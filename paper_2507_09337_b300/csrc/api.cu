@@ -120,8 +120,9 @@ orcha_status orcha_mesh_create(const orcha_mesh_desc* d, orcha_mesh** out) {
     if (st) return st;
     if (!d->state_dev[0] || !d->state_dev[1] || !d->dt_dev || d->state_dev[0] == d->state_dev[1])
         return fail(ORCHA_ERR_INVALID, "mesh_create: two distinct state buffers and dt_dev are required");
-    if (((uintptr_t)d->state_dev[0] | (uintptr_t)d->state_dev[1] | (uintptr_t)d->dt_dev) & 7)
-        return fail(ORCHA_ERR_INVALID, "mesh_create: buffers must be 8-byte aligned");
+    // the hydro kernels load x-neighbour pairs of the state as 16-byte vectors
+    if ((((uintptr_t)d->state_dev[0] | (uintptr_t)d->state_dev[1]) & 15) || ((uintptr_t)d->dt_dev & 7))
+        return fail(ORCHA_ERR_INVALID, "mesh_create: state buffers must be 16-byte aligned, dt_dev 8-byte aligned");
 
     orcha_mesh* m = new orcha_mesh();
     m->desc = *d;

@@ -340,33 +340,45 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
     // block's (x, y) index times the block stride plus the in-block offset of
     // the source column. Per plane only the z part is added (uniform over the
     // CTA). GATHER = false reads the padded block itself.
-    constexpr int KMAX = (R2N + NT - 1) / NT;
-    int bxy[KMAX], oxy[KMAX];             // source block's (x, y) index; in-block offset of the column
-    unsigned interior_mask = 0;           // bit k: cell k is an interior column of the tile
+    // Cells are loaded in x pairs (2q, 2q + 1); R2X is even, so a pair never
+    // straddles rows. When the two sources are consecutive (everywhere but a
+    // clamped outflow edge) the pair is one 16-byte load per variable: the
+    // first cell's padded x index is even (x0, the block size and the padded
+    // row length are even), so with 16-byte aligned state buffers the address
+    // is 16-byte aligned.
+    constexpr int R2P = R2N / 2;
+    constexpr int KMAX = (R2P + NT - 1) / NT;
+    int bxy[KMAX][2], oxy[KMAX][2];       // per cell of pair k: source block's (x, y) index; in-block column offset
+    unsigned interior_mask = 0;           // bit 2k + e: cell e of pair k is an interior column of the tile
+    unsigned contig_mask = 0;             // bit k: the sources of pair k are consecutive
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        const int c = tid + k * NT;
-        const int ci = c % R2X, cj = c / R2X;
-        int sbx = bc[0], sby = bc[1], sx = x0 + ci, sy = y0 + cj;
-        if (GATHER) {
-            const int l[2] = {x0 + ci - kGuard, y0 + cj - kGuard};
-            int sb[2], sl[2];
 #pragma unroll
-            for (int d = 0; d < 2; ++d) {
-                const int n = m.nb[d] * m.bs[d];
-                int gi = bc[d] * m.bs[d] + l[d];
-                if (l[d] < 0 || l[d] >= m.bs[d]) {
-                    if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
-                    else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+        for (int e = 0; e < 2; ++e) {
+            const int c = 2 * (tid + k * NT) + e;
+            const int ci = c % R2X, cj = c / R2X;
+            int sbx = bc[0], sby = bc[1], sx = x0 + ci, sy = y0 + cj;
+            if (GATHER) {
+                const int l[2] = {x0 + ci - kGuard, y0 + cj - kGuard};
+                int sb[2], sl[2];
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const int n = m.nb[d] * m.bs[d];
+                    int gi = bc[d] * m.bs[d] + l[d];
+                    if (l[d] < 0 || l[d] >= m.bs[d]) {
+                        if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+                        else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+                    }
+                    sb[d] = gi / m.bs[d];
+                    sl[d] = gi % m.bs[d] + kGuard;
                 }
-                sb[d] = gi / m.bs[d];
-                sl[d] = gi % m.bs[d] + kGuard;
+                sbx = sb[0]; sby = sb[1]; sx = sl[0]; sy = sl[1];
             }
-            sbx = sb[0]; sby = sb[1]; sx = sl[0]; sy = sl[1];
+            bxy[k][e] = sbx + m.nb[0] * sby;
+            oxy[k][e] = sy * px + sx;
+            if (ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2) interior_mask |= 1u << (2 * k + e);
         }
-        bxy[k] = sbx + m.nb[0] * sby;
-        oxy[k] = sy * px + sx;
-        if (ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2) interior_mask |= 1u << k;
+        if (bxy[k][1] == bxy[k][0] && oxy[k][1] == oxy[k][0] + 1) contig_mask |= 1u << k;
     }
     const int nbxy = m.nb[0] * m.nb[1];
     const int plane = py * px;
@@ -389,9 +401,9 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         zb = sbz * nbxy;
         zc = sz * plane;
     };
-    // source of R2 cell k of this thread in the plane with z part (zb, zc)
-    auto src_of = [&](int k, int zb, int zc) -> const double* {
-        return Uin + (long long)(bxy[k] + zb) * m.blk_stride + (oxy[k] + zc);
+    // source of cell e of pair k of this thread in the plane with z part (zb, zc)
+    auto src_of = [&](int k, int e, int zb, int zc) -> const double* {
+        return Uin + (long long)(bxy[k][e] + zb) * m.blk_stride + (oxy[k][e] + zc);
     };
     // Ask L2 for the source lines of plane pzi ahead of its load (no registers held).
     auto prefetch_plane = [&](int pzi) {
@@ -399,10 +411,14 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         plane_z(pzi, zb, zc);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (tid + k * NT >= R2N) break;
-            const double* src = src_of(k, zb, zc);
+            if (tid + k * NT >= R2P) break;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + v * vs));
+            for (int e = 0; e < 2; ++e) {
+                if (e == 1 && ((contig_mask >> k) & 1u)) break;     // same 16 bytes as cell 0
+                const double* src = src_of(k, e, zb, zc);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + v * vs));
+            }
         }
     };
     // L: primitives of plane pzi into its ring slot
@@ -414,18 +430,38 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         const bool zin = pzi >= 0 && pzi < bz;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int c = tid + k * NT;
-            if (c >= R2N) break;
-            const double* src = src_of(k, zb, zc);
-            T U[NV], W[NV], r;
+            const int q = tid + k * NT;
+            if (q >= R2P) break;
+            double u[2][NV];
+            const double* s0 = src_of(k, 0, zb, zc);
+            if (((contig_mask >> k) & 1u) && ((reinterpret_cast<uintptr_t>(s0) & 15u) == 0)) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = P<T>::in(src[v * vs]);
-            prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W, r, gm1);
+                for (int v = 0; v < NV; ++v) {
+                    const double2 d = *reinterpret_cast<const double2*>(s0 + v * vs);
+                    u[0][v] = d.x;
+                    u[1][v] = d.y;
+                }
+            } else {
+                const double* s1 = src_of(k, 1, zb, zc);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
-            P<T>::st(&w[NV * R2N + c], r);
-            if (zin && ((interior_mask >> k) & 1u) && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1])))
-                atomicOr(m.err, 1);
+                for (int v = 0; v < NV; ++v) {
+                    u[0][v] = s0[v * vs];
+                    u[1][v] = s1[v * vs];
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = 2 * q + e;
+                T U[NV], W[NV], r;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) U[v] = P<T>::in(u[e][v]);
+                prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W, r, gm1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
+                P<T>::st(&w[NV * R2N + c], r);
+                if (zin && ((interior_mask >> (2 * k + e)) & 1u) && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1])))
+                    atomicOr(m.err, 1);
+            }
         }
     };
 

@@ -87,6 +87,9 @@ def test_mesh_create_rejects_missing_buffers(L):
     d.state_dev[0], d.state_dev[1], d.dt_dev = 256, 516, 1024
     assert L.orcha_mesh_create(ctypes.byref(d), ctypes.byref(h)) == B.ORCHA_ERR_INVALID
     assert "aligned" in B.orcha_last_error()
+    d.state_dev[0], d.state_dev[1], d.dt_dev = 256, 520, 1024       # 8-byte but not 16-byte aligned
+    assert L.orcha_mesh_create(ctypes.byref(d), ctypes.byref(h)) == B.ORCHA_ERR_INVALID
+    assert "16-byte" in B.orcha_last_error()
 
 
 def test_null_handles_are_rejected(L):
