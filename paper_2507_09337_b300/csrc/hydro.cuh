@@ -449,18 +449,38 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                     u[1][v] = s1[v * vs];
                 }
             }
+            if constexpr (std::is_same<T, float>::value) {
+                // FP32: both cells' primitives and 1/rho, then one 8-byte store per array
+                // (the pair's slots are adjacent and 2-element aligned). Measured on a B300:
+                // FP32 flux +2.6 %; the FP64 and FF variants keep the per-cell stores
+                // (FF -1 % with the pair held in registers).
+                float W[2][NW];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int c = 2 * q + e;
-                T U[NV], W[NV], r;
+                for (int e = 0; e < 2; ++e) {
+                    float U[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) U[v] = P<T>::in(u[e][v]);
-                prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W, r, gm1);
+                    for (int v = 0; v < NV; ++v) U[v] = P<T>::in(u[e][v]);
+                    prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W[e], W[e][NV], gm1);
+                    if (zin && ((interior_mask >> (2 * k + e)) & 1u) && !(W[e][0] > 0.0f && W[e][NV - 1] > 0.0f))
+                        atomicOr(m.err, 1);
+                }
 #pragma unroll
-                for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
-                P<T>::st(&w[NV * R2N + c], r);
-                if (zin && ((interior_mask >> (2 * k + e)) & 1u) && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1])))
-                    atomicOr(m.err, 1);
+                for (int v = 0; v < NW; ++v)
+                    *reinterpret_cast<float2*>(&w[v * R2N + 2 * q]) = make_float2(W[0][v], W[1][v]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = 2 * q + e;
+                    T U[NV], W[NV], r;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) U[v] = P<T>::in(u[e][v]);
+                    prim_from_cons_as<Arith<T, 1>, T, NDIM>(U, W, r, gm1);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) P<T>::st(&w[v * R2N + c], W[v]);
+                    P<T>::st(&w[NV * R2N + c], r);
+                    if (zin && ((interior_mask >> (2 * k + e)) & 1u) && !(P<T>::pos(W[0]) && P<T>::pos(W[NV - 1])))
+                        atomicOr(m.err, 1);
+                }
             }
         }
     };
