@@ -8,7 +8,8 @@ per time step guard fill + hydro task on every packet + dt reduction, and
 unpack the result. Metric: zone-updates/s (interior cells x time steps / s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff|sedov128_rk2]
+                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff|sedov128_rk2|
+                     sedov128_rk2_f32|sedov128_rk2_ff]
                     [--no-cpu-baseline]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
@@ -40,6 +41,7 @@ FLOPS_PER_ZONE_3D = 462
 # states 45, HLL 3 x 86, update 45 each), the signal speed once (23) and the
 # stage combination 0.5 (U + U*) (10).
 FLOPS_PER_ZONE_3D_RK2 = 2 * (12 + 15 + 45 + 3 * 86 + 45) + 23 + 10
+BYTES_PER_ZONE_3D_RK2_STEP = 200         # stage 1: 40 B in + 40 B out; stage 2: 80 B in + 40 B out
 BYTES_PER_ZONE_3D = 80        # read U^n and write U^{n+1}: 5 vars x 8 B x 2
 FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 2032 MHz, non-FMA ops
 
@@ -78,7 +80,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sedov128",
                     choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff",
-                             "sedov128_rk2"])
+                             "sedov128_rk2", "sedov128_rk2_f32", "sedov128_rk2_ff"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-threads", type=int, default=0,
@@ -97,17 +99,20 @@ def workload(name):
         desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
         nt = 10
     task = "f32flux" if name.endswith("_f32") else "ff" if name.endswith("_ff") else "fp64"
-    if name.endswith("_rk2"):
+    if "_rk2" in name:
         import dataclasses
-        task = "rk2"
+        task = {"fp64": "rk2", "f32flux": "rk2_f32", "ff": "rk2_ff"}[task]
         spec = dataclasses.replace(spec, cfl=0.4)
         desc += "; Heun RK2 steps (two plain-MUSCL stages), CFL 0.4"
     return spec, packets, nt, task, desc
 
 
 DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 update",
-          "ff": "double-word f32x2 reconstruction/flux + f64 update", "rk2": "f64"}
-KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw", "rk2": "rd,true"}
+          "ff": "double-word f32x2 reconstruction/flux + f64 update", "rk2": "f64",
+          "rk2_f32": "f32 reconstruction/flux + f64 update (Heun RK2)",
+          "rk2_ff": "double-word f32x2 reconstruction/flux + f64 update (Heun RK2)"}
+KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw", "rk2": "rd,true", "rk2_f32": "float,true",
+          "rk2_ff": "dw,true"}
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -218,7 +223,7 @@ def run_reference(args):
     oracle.set_threads(threads)
     m = oracle.Mesh(**spec.oracle_kwargs())
     U = U0.copy()
-    step = oracle.step_rk2 if task == "rk2" else oracle.step
+    step = oracle.step_rk2 if task.startswith("rk2") else oracle.step
     for _ in range(args.warmup):
         U, _, _ = step(m, U, oracle.dt(m, U))
     t0 = time.perf_counter()
@@ -280,7 +285,7 @@ def main():
     batch = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
     hydro_events = []
     # per bench step: pack, signal speed (one launch), dt reduce, nt persistent launches, unpack
-    launches_per_step = 1 + 1 + 1 + nt * (2 if task_name == "rk2" else 1) + 1
+    launches_per_step = 1 + 1 + 1 + nt * (2 if task_name.startswith("rk2") else 1) + 1
 
     def step(record: bool):
         B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
@@ -351,13 +356,19 @@ def main():
     else:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
-        achieved = BYTES_PER_ZONE_3D * zones_per_launch / avg_launch_s / 1e9
+        # a Heun step is two launches: stage 1 reads and writes the state (80 B
+        # per zone), stage 2 also reads the step's initial state (120 B)
+        rk = task_name.startswith("rk2")
+        bytes_per_zone = BYTES_PER_ZONE_3D_RK2_STEP if rk else BYTES_PER_ZONE_3D
+        achieved = bytes_per_zone * zones_per_launch / avg_launch_s / 1e9
         kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
         prof = {"sedov128_f32": "persistent_kernel_f32flux_sedov128.md",
                 "sedov128_ff": "persistent_kernel_ff_sedov128.md"}.get(args.workload)
         traffic = profiled_traffic(prof, kname) if prof else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": kname}
+        if rk:
+            roof["per_launch"] = "one time step of all packets (two stage launches)"
     hbm_peak = 6489.3
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]

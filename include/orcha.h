@@ -119,7 +119,19 @@ typedef enum {
     ORCHA_TASK_RK2_STAGE2 = 6,
     /* For orcha_mesh_advance, orcha_batch_advance and orcha_autotune: whole
      * Heun steps (stage 1, swap, guard fill, stage 2, dt reduce, swap). */
-    ORCHA_TASK_HYDRO_RK2 = 7
+    ORCHA_TASK_HYDRO_RK2 = 7,
+    /* The two Heun stages and the whole Heun step with the plain MUSCL
+     * operator evaluated as in HYDRO_F32FLUX (FP32 primitives, slopes and HLL
+     * fluxes, float-float flux sums, FP64 update, stage-2 average and dt; the
+     * step's first dt by the FP32 signal-speed rule). */
+    ORCHA_TASK_RK2_F32FLUX_STAGE1 = 8,
+    ORCHA_TASK_RK2_F32FLUX_STAGE2 = 9,
+    ORCHA_TASK_HYDRO_RK2_F32FLUX = 10,
+    /* The same with the operator evaluated as in HYDRO_FF (double-word
+     * arithmetic on the FP32 pipe, FP64 update, stage-2 average and dt). */
+    ORCHA_TASK_RK2_FF_STAGE1 = 11,
+    ORCHA_TASK_RK2_FF_STAGE2 = 12,
+    ORCHA_TASK_HYDRO_RK2_FF = 13
 } orcha_task;
 
 /* Mesh geometry and the caller's device buffers. */

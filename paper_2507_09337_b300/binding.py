@@ -37,13 +37,19 @@ ORCHA_TASK_HYDRO_FF = 4
 ORCHA_TASK_RK2_STAGE1 = 5
 ORCHA_TASK_RK2_STAGE2 = 6
 ORCHA_TASK_HYDRO_RK2 = 7
+ORCHA_TASK_RK2_F32FLUX_STAGE1 = 8
+ORCHA_TASK_RK2_F32FLUX_STAGE2 = 9
+ORCHA_TASK_HYDRO_RK2_F32FLUX = 10
+ORCHA_TASK_RK2_FF_STAGE1 = 11
+ORCHA_TASK_RK2_FF_STAGE2 = 12
+ORCHA_TASK_HYDRO_RK2_FF = 13
 
 ORCHA_INIT_FROM_HOST = 0
 ORCHA_INIT_SPHERE = 1
 ORCHA_INIT_HALF_SPACE = 2
 
 TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF,
-         "rk2": ORCHA_TASK_HYDRO_RK2}
+         "rk2": ORCHA_TASK_HYDRO_RK2, "rk2_f32": ORCHA_TASK_HYDRO_RK2_F32FLUX, "rk2_ff": ORCHA_TASK_HYDRO_RK2_FF}
 
 
 class OrchaError(RuntimeError):

@@ -337,6 +337,10 @@ orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
         case ORCHA_TASK_HYDRO_FF:
         case ORCHA_TASK_RK2_STAGE1:
         case ORCHA_TASK_RK2_STAGE2:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE1:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE2:
+        case ORCHA_TASK_RK2_FF_STAGE1:
+        case ORCHA_TASK_RK2_FF_STAGE2:
             e = orcha::launch_hydro(m->dev, m->tile_x, m->tile_y, orcha::prec_of(task), p->ids_dev, p->n, cur, nxt,
                                     orcha::stage_of(task), st);
             break;
@@ -360,14 +364,14 @@ static orcha_status enqueue_steps(orcha_mesh* m, orcha_packet* const* pk, int np
     if (init_dt) {
         // the packets cover every block: one launch over the whole mesh
         ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], (cudaStream_t)stream,
-                                                  orcha::prec_of(task) == orcha::kF32),
+                                                  orcha::prec_f32_dt(orcha::prec_of(task))),
                    "advance signal speed");
         if ((s = orcha_dt_reduce(m, stream))) return s;
     }
     // a Heun step is two sweeps (stage 1, swap, stage 2, swap), every other
     // step one; each sweep refreshes the guards of the state it reads
-    const bool rk = task == ORCHA_TASK_HYDRO_RK2;
-    const orcha_task sweeps[2] = {rk ? ORCHA_TASK_RK2_STAGE1 : task, ORCHA_TASK_RK2_STAGE2};
+    const bool rk = orcha::is_rk_step_task(task);
+    const orcha_task sweeps[2] = {rk ? orcha::rk_stage_task(task, 1) : task, orcha::rk_stage_task(task, 2)};
     for (int n = 0; n < nsteps; ++n) {
         for (int k = 0; k < (rk ? 2 : 1); ++k) {
             for (int i = 0; i < npk; ++i)
@@ -403,7 +407,7 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
         if (g.task == task && g.nsteps == nsteps && g.init_dt == init_dt && g.start_cur == start &&
             g.packets.size() == (size_t)npk && std::equal(g.packets.begin(), g.packets.end(), pk)) {
             ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
-            m->cur = start ^ ((task == ORCHA_TASK_HYDRO_RK2 ? 0 : nsteps) & 1);
+            m->cur = start ^ ((orcha::is_rk_step_task(task) ? 0 : nsteps) & 1);
             return ORCHA_OK;
         }
     }
@@ -425,7 +429,7 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     m->graphs.push_back(g);
     ORCHA_CUDA(cudaGraphLaunch(g.exec, st), "mesh_advance graph launch");
-    m->cur = start ^ ((task == ORCHA_TASK_HYDRO_RK2 ? 0 : nsteps) & 1);
+    m->cur = start ^ ((orcha::is_rk_step_task(task) ? 0 : nsteps) & 1);
     return ORCHA_OK;
 }
 
@@ -524,6 +528,7 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
 // measured per variant on a B300 (128^3 Sedov: FP64 halves beat thirds by
 // 1.5 %, FF thirds beat halves by 3.6 %, FP32 flux no difference).
 static orcha_status ensure_list(orcha_batch* b, int prec) {
+    if (prec < 0 || prec >= orcha::kNumPrec) return fail(ORCHA_ERR_INVALID, "batch: not a hydro task variant");
     orcha_batch::List& L = b->lists[prec];
     if (L.built) return ORCHA_OK;
     int per_sm = 0;
@@ -539,7 +544,7 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
         std::vector<orcha::Item> slabs;
         for (auto it : tail) {
             const int bz = b->meshes[it.slot]->dev.bs[2];
-            const int s_max = prec == orcha::kFF ? 8 : 2;
+            const int s_max = orcha::prec_is_dw(prec) ? 8 : 2;
             const int s = (int)std::min<long long>(std::min<long long>(G / R, bz / 4), s_max);
             if (s >= 2) {
                 for (int k = 0; k < s; ++k) {
@@ -586,7 +591,7 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
 static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, cudaStream_t st) {
     const int prec = orcha::prec_of(task);
     const orcha_batch::List& L = b->lists[prec];
-    const int stages = task == ORCHA_TASK_HYDRO_RK2 ? 2 : 1;     // a Heun step is two launches
+    const int stages = orcha::is_rk_step_task(task) ? 2 : 1;     // a Heun step is two launches
     for (int n = 0; n < nsteps; ++n) {
         for (int k = 1; k <= stages; ++k) {
             ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
@@ -610,7 +615,7 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
         // one launch per mesh over all its blocks (the batch covers every block)
         for (auto* m : b->meshes) {
             ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st,
-                                                      orcha::prec_of(task) == orcha::kF32),
+                                                      orcha::prec_f32_dt(orcha::prec_of(task))),
                        "batch signal speed");
             if ((s = orcha_dt_reduce(m, stream))) return s;
         }
@@ -642,7 +647,7 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
         }
         ORCHA_CUDA(cudaGraphLaunch(exec, st), "batch graph launch");
     }
-    const int flips = nsteps * (task == ORCHA_TASK_HYDRO_RK2 ? 2 : 1);     // one per launch
+    const int flips = nsteps * (orcha::is_rk_step_task(task) ? 2 : 1);     // one per launch
     for (auto* m : b->meshes) m->cur ^= (flips & 1);
     return ORCHA_OK;
 }

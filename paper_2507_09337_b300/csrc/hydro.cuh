@@ -739,8 +739,9 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                         const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
                         const rd acc = rd(acc_prev[v]) + tz;
                         Un[v] = rd(Ub[gi + v * vs]) - acc;
-                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     }
+                    // Heun stage 2: the average with the step's initial state, in FP64
+                    if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
                 if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
@@ -776,10 +777,8 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 for (int v = 0; v < NV; ++v) {
                     if constexpr (F32) Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(acc_ff[v]));
                     else if constexpr (DW) Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v]));
-                    else {
-                        Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
-                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
-                    }
+                    else Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
+                    if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
                 if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));

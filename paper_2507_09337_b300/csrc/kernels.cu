@@ -406,7 +406,7 @@ cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigne
 
 // ---------------------------------------------------------------- hydro launch table
 // Variant of a precision code: arithmetic type and whether the kernel runs
-// Runge-Kutta stages (kRK2: FP64, plain MUSCL).
+// Runge-Kutta stages (plain MUSCL; kRK2 FP64, kRK2F32 FP32 flux, kRK2FF double-word).
 template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,
                                   int stage, cudaStream_t st) {
@@ -451,6 +451,8 @@ static cudaError_t occupancy_t(int* per_sm) {
         return prec == kF32   ? launch_persistent_t<ND, X, Y, float, false>(slots, items, nitems, queue, grid, 0, st) \
                : prec == kFF  ? launch_persistent_t<ND, X, Y, dw, false>(slots, items, nitems, queue, grid, 0, st)    \
                : prec == kRK2 ? launch_persistent_t<ND, X, Y, rd, true>(slots, items, nitems, queue, grid, stage, st) \
+               : prec == kRK2F32 ? launch_persistent_t<ND, X, Y, float, true>(slots, items, nitems, queue, grid, stage, st) \
+               : prec == kRK2FF ? launch_persistent_t<ND, X, Y, dw, true>(slots, items, nitems, queue, grid, stage, st) \
                               : launch_persistent_t<ND, X, Y, rd, false>(slots, items, nitems, queue, grid, 0, st);
 
 cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
@@ -469,6 +471,8 @@ cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev*
         return prec == kF32   ? occupancy_t<ND, X, Y, float, false>(per_sm)                            \
                : prec == kFF  ? occupancy_t<ND, X, Y, dw, false>(per_sm)                               \
                : prec == kRK2 ? occupancy_t<ND, X, Y, rd, true>(per_sm)                                \
+               : prec == kRK2F32 ? occupancy_t<ND, X, Y, float, true>(per_sm)                          \
+               : prec == kRK2FF ? occupancy_t<ND, X, Y, dw, true>(per_sm)                              \
                               : occupancy_t<ND, X, Y, rd, false>(per_sm);
 
 cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm) {
@@ -486,6 +490,8 @@ cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm
         return prec == kF32   ? launch_hydro_t<ND, X, Y, float, false>(m, ids, n, Uin, Uout, 0, st)    \
                : prec == kFF  ? launch_hydro_t<ND, X, Y, dw, false>(m, ids, n, Uin, Uout, 0, st)       \
                : prec == kRK2 ? launch_hydro_t<ND, X, Y, rd, true>(m, ids, n, Uin, Uout, stage, st)    \
+               : prec == kRK2F32 ? launch_hydro_t<ND, X, Y, float, true>(m, ids, n, Uin, Uout, stage, st) \
+               : prec == kRK2FF ? launch_hydro_t<ND, X, Y, dw, true>(m, ids, n, Uin, Uout, stage, st)  \
                               : launch_hydro_t<ND, X, Y, rd, false>(m, ids, n, Uin, Uout, 0, st);
 
 cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
@@ -505,6 +511,8 @@ cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* 
         cudaError_t e = configure_t<ND, X, Y, float, false>();                                         \
         if (e == cudaSuccess) e = configure_t<ND, X, Y, dw, false>();                                  \
         if (e == cudaSuccess) e = configure_t<ND, X, Y, rd, true>();                                   \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, float, true>();                                \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, dw, true>();                                   \
         return e != cudaSuccess ? e : configure_t<ND, X, Y, rd, false>();                              \
     }
 

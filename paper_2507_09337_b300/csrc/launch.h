@@ -11,9 +11,14 @@ namespace orcha {
 
 // Variants of the hydro kernels: MUSCL-Hancock steps in FP64, with FP32
 // reconstruction/flux or with double-word reconstruction/flux (all with the
-// FP64 update), and Heun Runge-Kutta stages (plain MUSCL, FP64).
-enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3 };
-constexpr int kNumPrec = 4;
+// FP64 update), and Heun Runge-Kutta stages (plain MUSCL) in the same three
+// arithmetics.
+enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3, kRK2F32 = 4, kRK2FF = 5 };
+constexpr int kNumPrec = 6;
+inline bool prec_is_rk(int p) { return p == kRK2 || p == kRK2F32 || p == kRK2FF; }
+// variants whose first dt uses the FP32 signal-speed rule
+inline bool prec_f32_dt(int p) { return p == kF32 || p == kRK2F32; }
+inline bool prec_is_dw(int p) { return p == kFF || p == kRK2FF; }
 // Variant of a hydro task, or -1 for any other task.
 inline int prec_of(orcha_task t) {
     switch (t) {
@@ -23,17 +28,41 @@ inline int prec_of(orcha_task t) {
         case ORCHA_TASK_HYDRO_RK2:
         case ORCHA_TASK_RK2_STAGE1:
         case ORCHA_TASK_RK2_STAGE2: return kRK2;
+        case ORCHA_TASK_HYDRO_RK2_F32FLUX:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE1:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE2: return kRK2F32;
+        case ORCHA_TASK_HYDRO_RK2_FF:
+        case ORCHA_TASK_RK2_FF_STAGE1:
+        case ORCHA_TASK_RK2_FF_STAGE2: return kRK2FF;
         default: return -1;
     }
 }
 // Runge-Kutta stage of a packet task (1 or 2), 0 for a whole-step task.
 inline int stage_of(orcha_task t) {
-    return t == ORCHA_TASK_RK2_STAGE1 ? 1 : t == ORCHA_TASK_RK2_STAGE2 ? 2 : 0;
+    switch (t) {
+        case ORCHA_TASK_RK2_STAGE1:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE1:
+        case ORCHA_TASK_RK2_FF_STAGE1: return 1;
+        case ORCHA_TASK_RK2_STAGE2:
+        case ORCHA_TASK_RK2_F32FLUX_STAGE2:
+        case ORCHA_TASK_RK2_FF_STAGE2: return 2;
+        default: return 0;
+    }
+}
+// Whole Heun-step tasks (two launches per step).
+inline bool is_rk_step_task(orcha_task t) {
+    return t == ORCHA_TASK_HYDRO_RK2 || t == ORCHA_TASK_HYDRO_RK2_F32FLUX || t == ORCHA_TASK_HYDRO_RK2_FF;
+}
+// Packet task of stage k (1 or 2) of a whole Heun-step task.
+inline orcha_task rk_stage_task(orcha_task step, int k) {
+    if (step == ORCHA_TASK_HYDRO_RK2_F32FLUX) return k == 1 ? ORCHA_TASK_RK2_F32FLUX_STAGE1 : ORCHA_TASK_RK2_F32FLUX_STAGE2;
+    if (step == ORCHA_TASK_HYDRO_RK2_FF) return k == 1 ? ORCHA_TASK_RK2_FF_STAGE1 : ORCHA_TASK_RK2_FF_STAGE2;
+    return k == 1 ? ORCHA_TASK_RK2_STAGE1 : ORCHA_TASK_RK2_STAGE2;
 }
 // Tasks that advance whole steps (mesh_advance, batch_advance, autotune).
 inline bool is_step_task(orcha_task t) {
     return t == ORCHA_TASK_HYDRO_FP64 || t == ORCHA_TASK_HYDRO_F32FLUX || t == ORCHA_TASK_HYDRO_FF ||
-           t == ORCHA_TASK_HYDRO_RK2;
+           is_rk_step_task(t);
 }
 
 // Error reporting of the C ABI (sets the calling thread's orcha_last_error).
@@ -44,7 +73,7 @@ orcha_status cuda_error(cudaError_t e, const char* what);
 orcha_status mesh_dev_from_desc(const orcha_mesh_desc* d, MeshDev* out, long long* nblk_out);
 
 // One hydro launch over the packet blocks ids[0..n); stage: Runge-Kutta stage
-// (1 or 2) for kRK2, else 0.
+// (1 or 2) for the Runge-Kutta variants, else 0.
 cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* ids, int n, const double* Uin,
                          double* Uout, int stage, cudaStream_t st);
 bool hydro_tile_supported(int ndim, int tx, int ty);

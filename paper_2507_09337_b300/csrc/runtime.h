@@ -7,6 +7,7 @@
 #include "../../include/orcha.h"
 #include "common.cuh"
 #include "persistent.cuh"
+#include "launch.h"
 
 namespace orcha {
 
@@ -54,7 +55,7 @@ struct orcha_batch {
         orcha::Item* items_dev = nullptr;
         orcha::SlotDev* slots_dev = nullptr;
         unsigned* done_dev = nullptr;
-    } lists[4];                                      // indexed by orcha::Prec (kNumPrec = 4)
+    } lists[orcha::kNumPrec];                        // indexed by orcha::Prec
     unsigned* queue = nullptr;
     int* cur_dev = nullptr;
     int num_sms = 0;
