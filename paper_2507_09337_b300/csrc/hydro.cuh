@@ -265,7 +265,7 @@ struct Tile {
     static constexpr int NSLOT = (NDIM == 3) ? 3 : 1;
     template <class S>
     static constexpr size_t smem_bytes() {
-        return sizeof(S) * ((size_t)NSLOT * NW * R2N + 4 * NV * R1N + NV * (NXF + NYF));
+        return sizeof(S) * ((size_t)NSLOT * NW * R2N + 4 * NV * R1N);
     }
 };
 
@@ -296,8 +296,12 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
 
     S* sW = reinterpret_cast<S*>(smem_raw);                 // [slot][NW][R2N]
     S* sFS = sW + Tl::NSLOT * NW * R2N;                    // [face 0..3 = x-,x+,y-,y+][NV][R1N]
-    S* sFx = sFS + 4 * NV * R1N;                           // [NV][NXF]
-    S* sFy = sFx + NV * Tl::NXF;                           // [NV][NYF]
+    // Face fluxes overwrite the x+ / y+ face states they were formed from: the
+    // left state of each x (y) face is read by that face's thread alone, before
+    // it stores the flux. The flux of the x face on the high side of R1 cell i
+    // is at sGx[v * R1N + i], that of the y face likewise in sGy.
+    S* sGx = sFS + 1 * NV * R1N;
+    S* sGy = sFS + 3 * NV * R1N;
 
     const int tid = threadIdx.x;
     const int px = m.pad[0], py = m.pad[1];
@@ -697,8 +701,8 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                     R[v] = P<T>::ld(&sFS[(fR * NV + src) * R1N + iR]);
                 }
                 hll<T, NDIM, false>(L, R, F, g, igm1);
-                S* dst = (nrm == 0) ? (sFx + f) : (sFy + (f - Tl::NXF));
-                const int stride = (nrm == 0) ? Tl::NXF : Tl::NYF;
+                S* dst = ((nrm == 0) ? sGx : sGy) + iL;
+                const int stride = R1N;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     int dv = v;
@@ -751,22 +755,22 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         }
         if (inner) {
             // x then y flux differences of plane p
-            const int fx = tj * (TX + 1) + ti, fy = tj * TX + ti;
+            // high x face of the cell at o1, low x face at o1 - 1; high y face at o1, low at o1 - R1X
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if constexpr (F32) {
-                    const ff tx = ff_scale(ff_diff(sFx[v * Tl::NXF + fx + 1], sFx[v * Tl::NXF + fx]), ch[0], cl[0]);
-                    const ff ty = ff_scale(ff_diff(sFy[v * Tl::NYF + fy + TX], sFy[v * Tl::NYF + fy]), ch[1], cl[1]);
+                    const ff tx = ff_scale(ff_diff(sGx[v * R1N + o1], sGx[v * R1N + o1 - 1]), ch[0], cl[0]);
+                    const ff ty = ff_scale(ff_diff(sGy[v * R1N + o1], sGy[v * R1N + o1 - R1X]), ch[1], cl[1]);
                     acc_ff[v] = ff_add(tx, ty);
                 } else if constexpr (DW) {
-                    const dw tx = cdw[0] * (P<T>::ld(&sFx[v * Tl::NXF + fx + 1]) - P<T>::ld(&sFx[v * Tl::NXF + fx]));
-                    const dw ty = cdw[1] * (P<T>::ld(&sFy[v * Tl::NYF + fy + TX]) - P<T>::ld(&sFy[v * Tl::NYF + fy]));
+                    const dw tx = cdw[0] * (P<T>::ld(&sGx[v * R1N + o1]) - P<T>::ld(&sGx[v * R1N + o1 - 1]));
+                    const dw ty = cdw[1] * (P<T>::ld(&sGy[v * R1N + o1]) - P<T>::ld(&sGy[v * R1N + o1 - R1X]));
                     acc_dw[v] = tx + ty;
                 } else {
-                    const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx + 1]))) -
-                                               rd(P<T>::to_double(P<T>::ld(&sFx[v * Tl::NXF + fx]))));
-                    const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy + TX]))) -
-                                               rd(P<T>::to_double(P<T>::ld(&sFy[v * Tl::NYF + fy]))));
+                    const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1]))) -
+                                               rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1 - 1]))));
+                    const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1]))) -
+                                               rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1 - R1X]))));
                     acc_prev[v] = (tx + ty).v;
                 }
             }
