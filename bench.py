@@ -51,11 +51,24 @@ KERNEL_SOURCES = ["paper_2507_09337_b300/csrc/common.cuh", "paper_2507_09337_b30
                   "paper_2507_09337_b300/csrc/softfp64.cuh"]
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the kernel sources' code: comments and whitespace are
+    removed first, so editing a comment does not void a recorded capture."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        src = open(os.path.join(ROOT, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
+    return h.hexdigest()
+
+
 def profiled_traffic(profile_md: str, kernel: str):
     """DRAM bytes per launch from a committed ncu summary, or None if the
-    summary covers another kernel variant or the kernel sources changed since
+    summary covers another kernel variant or the kernel code changed since
     that capture (hash mismatch)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", profile_md)
     if not os.path.exists(path):
         return None
@@ -64,10 +77,7 @@ def profiled_traffic(profile_md: str, kernel: str):
         if ":" in line and line.startswith("    "):
             k, v = line.strip().split(":", 1)
             fields[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if fields.get("kernel_source_sha256") != h.hexdigest() or fields.get("kernel") != kernel:
+    if fields.get("kernel_source_sha256") != kernel_source_hash() or fields.get("kernel") != kernel:
         return None
     return float(fields["traffic_bytes_per_launch"])
 

@@ -16,11 +16,13 @@
 // GPU mapping. One CTA owns a TX x TY column tile of one block and sweeps it
 // along z (2.5D blocking), one thread per interior column. Per plane:
 //   L  primitives of the (TX+4)(TY+4) plane two layers ahead into a ring of
-//      three planes in shared memory (the z stencil needs p-1, p, p+1);
+//      three planes in shared memory (the z stencil needs p-1, p, p+1), read
+//      as 16-byte pairs of x-neighbours;
 //   P  slopes, predictor and face states of plane p: interior cells by their
 //      owner thread (z face states stay in its registers), the one-cell ring
 //      around the tile by the first 2(TX+TY) threads (x/y face states only);
-//   F  every x and y face flux of plane p once, into shared memory;
+//   F  every x and y face flux of plane p once, into shared memory over the
+//      face state it was formed from;
 //   U  each owner forms its z face flux from registers, finishes the update
 //      of plane p-1 (whose z fluxes are now both known) and writes it.
 // Every face flux is evaluated exactly once per CTA and used by both cells,
