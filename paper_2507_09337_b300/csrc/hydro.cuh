@@ -273,9 +273,12 @@ struct Tile {
 
 // One column tile of one block: the z sweep over interior planes [z0, z1)
 // (default: the whole block; a sub-range recomputes its own z halo, so a
-// block may be advanced as several z slabs with the same result bits).
-// Returns this thread's
-// largest signal speed of the new state (0 for threads without cells).
+// block may be advanced as several z slabs with the same result bits). With
+// GATHER the range may run on through the blocks above blk in the same
+// column (plane q lies in block blk + (q / bz) nb_x nb_y), so one sweep
+// covers several blocks with one z halo. Each block's largest signal speed
+// of the new state is raised (atomicMax into m.smax, using the CTA scratch
+// red) when the sweep leaves that block or the range ends.
 // GATHER = false: guard cells are read from the padded block (filled by the
 // guard-fill task). GATHER = true: guard cells are read straight from the
 // source cell (a neighbour's interior, or the boundary rule's cell), so no
@@ -288,9 +291,10 @@ struct Tile {
 // (Uin + dt L(Uin))), the old Uout (the step's initial state) read at the
 // cell just before it is overwritten. Stage 1 raises no signal speed.
 template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false>
-__device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
-                                             const double* __restrict__ Uin, double* __restrict__ Uout,
-                                             unsigned char* smem_raw, int z0 = 0, int z1 = -1, int stage = 0) {
+__device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
+                                           const double* __restrict__ Uin, double* __restrict__ Uout,
+                                           unsigned char* smem_raw, unsigned long long* red, int z0 = 0,
+                                           int z1 = -1, int stage = 0) {
     using Tl = Tile<NDIM, TX, TY>;
     using S = typename P<T>::store;
     constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
@@ -433,7 +437,7 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
         S* w = sW + slot * NW * R2N;
         int zb, zc;
         plane_z(pzi, zb, zc);
-        const bool zin = pzi >= 0 && pzi < bz;
+        const bool zin = pzi >= z0 && pzi < z1;        // planes this item owns: each cell checked once
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int q = tid + k * NT;
@@ -730,8 +734,10 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                 Fz[0] = F[0]; Fz[3] = F[1]; Fz[1] = F[2]; Fz[2] = F[3]; Fz[4] = F[4];
             }
             if (p >= z0 + 1) {
-                const int q = p - 1;
-                const long long gi = ((long long)(q + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                // plane q of the column: block qb above blk, in-block plane ql
+                const int q = p - 1, qb = q / bz, ql = q - qb * bz;
+                const long long gi = (long long)qb * nbxy * m.blk_stride +
+                                     ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
                 rd Un[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -750,7 +756,14 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
                     if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                if (!RK || stage == 2) {
+                    smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                    // leaving a block (or the item's range): raise its signal speed (CTA-uniform)
+                    if (q == z1 - 1 || ql == bz - 1) {
+                        cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
+                        smaxb = 0ull;
+                    }
+                }
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
@@ -791,7 +804,9 @@ __device__ __forceinline__ double hydro_tile(const MeshDev& m, const int blk, co
             }
         }
     }
-    return __longlong_as_double((long long)smaxb);
+    if constexpr (NDIM == 2) {
+        if (!RK || stage == 2) cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
+    }
 }
 
 // Packet path: one CTA per (packet block, column tile); guards come from the
@@ -805,9 +820,8 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
     const int ntile = tiles_x * tiles_y;
     const int blk = blk_ids[blockIdx.x / ntile];
     const int tile = blockIdx.x % ntile;
-    const double s = hydro_tile<NDIM, TX, TY, T, false, RK>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY,
-                                                            Uin, Uout, smem_raw, 0, -1, stage);
-    if (!RK || stage == 2) cta_raise_smax(s, red, &m.smax[blk]);     // uniform over the CTA
+    hydro_tile<NDIM, TX, TY, T, false, RK>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY, Uin, Uout,
+                                           smem_raw, red, 0, -1, stage);
 }
 
 }  // namespace orcha

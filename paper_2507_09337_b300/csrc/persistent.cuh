@@ -34,8 +34,9 @@ struct SlotDev {
     int tiles_x, tiles_y;
 };
 
-// One unit of work: a column tile of a block, over the interior planes
-// [z0, z1) when zr = z0 | z1 << 8 is non-zero, else over the whole block.
+// One unit of work: a column tile of block blk over its interior planes, or,
+// when zr = z0 | z1 << 16 is non-zero, over the planes [z0, z1) of the
+// column of blocks above blk (plane q lies in block blk + (q / bz) nb_x nb_y).
 struct Item {
     int slot, blk, tile, zr;
 };
@@ -92,11 +93,9 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         const Item w = items[it];
         const SlotDev& sd = slots[w.slot];
         const int cur = __ldcg(sd.cur);
-        const int z0 = w.zr ? (w.zr & 0xFF) : 0, z1 = w.zr ? (w.zr >> 8) : -1;
-        const double s = hydro_tile<NDIM, TX, TY, T, true, RK>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
-                                                               (w.tile / sd.tiles_x) * TY, sd.state[cur],
-                                                               sd.state[cur ^ 1], smem_raw, z0, z1, stage);
-        if (!RK || stage == 2) cta_raise_smax(s, red, &sd.m.smax[w.blk]);     // uniform over the CTA
+        const int z0 = w.zr ? (w.zr & 0xFFFF) : 0, z1 = w.zr ? (w.zr >> 16) : -1;
+        hydro_tile<NDIM, TX, TY, T, true, RK>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX, (w.tile / sd.tiles_x) * TY,
+                                              sd.state[cur], sd.state[cur ^ 1], smem_raw, red, z0, z1, stage);
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned d = atomicAdd(sd.done, 1u);
