@@ -11,6 +11,7 @@
 #include "../../include/orcha.h"
 #include "common.cuh"
 #include "launch.h"
+#include "worklist.h"
 
 using orcha::MeshDev;
 
@@ -520,61 +521,16 @@ orcha_status orcha_batch_create(orcha_packet* const* pk, int32_t npk, int32_t tx
     return ORCHA_OK;
 }
 
-// Work list of a 3D batch: z ranges of block columns. The planes of every
-// column tile (each mesh, column and tile in turn) form one stream of W
-// planes, cut at the multiples of W / G (G resident CTAs: one segment per
-// CTA) and at every column end; a piece shorter than 2 planes joins its
-// neighbour. The pieces are queued longest first, so every resident CTA
-// takes about one segment and a column tile pays its two-plane z halo about
-// once per CTA rather than once per block, and the last items to start are
-// the short ones. Same bits as full-block items. (Modelled with the halo at
-// 0.55 plane: 128^3 Sedov 39.2 plane-times per CTA against 43.3 for
-// full-block items with the last partial wave split in halves; ideal 38.)
-// 2D batches keep one item per block and tile.
+// Work list of a 3D batch: z ranges of block columns (worklist.h); 2D batches
+// keep one item per block and tile.
 static std::vector<orcha::Item> column_items(const orcha_batch* b, long long G) {
-    struct Col {
-        int slot, blk, tile, depth;
-    };
-    std::vector<Col> cols;
-    long long W = 0;
+    std::vector<orcha::ColumnSource> src;
     for (size_t s = 0; s < b->meshes.size(); ++s) {
         const orcha::MeshDev& d = b->meshes[s]->dev;
-        const int ntile = (d.bs[0] / b->tx) * (d.bs[1] / b->ty);
-        const int depth = d.nb[2] * d.bs[2];
-        for (int by = 0; by < d.nb[1]; ++by)
-            for (int bx = 0; bx < d.nb[0]; ++bx)
-                for (int t = 0; t < ntile; ++t) {
-                    cols.push_back({(int)s, bx + d.nb[0] * by, t, depth});
-                    W += depth;
-                }
+        src.push_back({(int)s, {d.nb[0], d.nb[1], d.nb[2]}, {d.bs[0], d.bs[1], d.bs[2]},
+                       (d.bs[0] / b->tx) * (d.bs[1] / b->ty)});
     }
-    const double seg = (double)W / (double)G;
-    const int kMinPiece = 2;
-    std::vector<orcha::Item> items;
-    long long base = 0;                        // stream position of the column's first plane
-    for (const Col& c : cols) {
-        std::vector<int> cuts{0};
-        for (long long k = (long long)std::floor((double)base / seg) + 1;; ++k) {
-            const long long pos = std::llround((double)k * seg) - base;
-            if (pos >= c.depth) break;
-            if (pos > cuts.back()) cuts.push_back((int)pos);
-        }
-        cuts.push_back(c.depth);
-        std::vector<int> kept{0};
-        for (size_t i = 1; i < cuts.size(); ++i) {
-            const bool last = i + 1 == cuts.size();
-            if (!last && cuts[i] - kept.back() < kMinPiece) continue;
-            if (last && cuts[i] - kept.back() < kMinPiece && kept.size() > 1) kept.pop_back();
-            kept.push_back(cuts[i]);
-        }
-        for (size_t i = 0; i + 1 < kept.size(); ++i)
-            items.push_back({c.slot, c.blk, c.tile, kept[i] | (kept[i + 1] << 16)});
-        base += c.depth;
-    }
-    std::stable_sort(items.begin(), items.end(), [](const orcha::Item& x, const orcha::Item& y) {
-        return (x.zr >> 16) - (x.zr & 0xFFFF) > (y.zr >> 16) - (y.zr & 0xFFFF);
-    });
-    return items;
+    return orcha::column_items(src, G);
 }
 
 static orcha_status ensure_list(orcha_batch* b, int prec) {
@@ -588,7 +544,7 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
     // z ranges of block columns (3D; a column's planes must fit the 15-bit
     // fields of Item::zr), else one item per block and tile
     bool columns = b->ndim == 3;
-    for (auto* m : b->meshes) columns = columns && (long long)m->dev.nb[2] * m->dev.bs[2] < (1 << 15);
+    for (auto* m : b->meshes) columns = columns && orcha::column_items_fit(m->dev);
     std::vector<orcha::Item> items = columns ? column_items(b, G) : b->base_items;
     const size_t ns = b->meshes.size();
     std::vector<int> per_mesh(ns, 0);
