@@ -69,10 +69,12 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // Resident CTAs per SM requested from the register allocator (A/B-measured
 // on a B300): the FP64 variant, bound by the FP64 pipe, gains from 384
 // threads per SM (a small spill; +2 %); the FP32-flux variant runs best at
-// 640 threads per SM (96 registers, a small spill: +5.6 % over 512; 768 and
-// more lose to the spills). The double-word variant has the FP64 variant's
-// register and shared-memory footprint (8-byte values) and takes its bound.
-template <class T, int NT> struct MinBlocks { static constexpr int value = (640 / NT) > 1 ? (640 / NT) : 1; };
+// 768 threads per SM for 16x8 and 16x16 tiles (80 registers, a 20-byte
+// spill: +4.8 % and +19 % over 640; six 16x8 CTAs is also what its shared
+// memory allows) and at 640 for 8x8 tiles (768 loses 12 %). The double-word
+// variant has the FP64 variant's register and shared-memory footprint
+// (8-byte values) and takes its bound.
+template <class T, int NT> struct MinBlocks { static constexpr int value = NT <= 64 ? 640 / NT : 768 / NT; };
 template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
 
