@@ -73,10 +73,13 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // spill: +4.8 % and +19 % over 640; six 16x8 CTAs is also what its shared
 // memory allows) and at 640 for 8x8 tiles (768 loses 12 %). The double-word
 // variant has the FP64 variant's register and shared-memory footprint
-// (8-byte values) and takes its bound.
+// (8-byte values) and takes its bound. Both run 16x16 tiles at two CTAs per
+// SM (128 registers, a ~100-byte spill; two 109 KB tiles fill the SM's
+// shared memory): FP64 +8 % and FF +27 % over one CTA, which makes 16x16
+// their fastest tile (FP64 +2.2 %, FF +9 % over 16x8).
 template <class T, int NT> struct MinBlocks { static constexpr int value = NT <= 64 ? 640 / NT : 768 / NT; };
-template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
-template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = (384 / NT) > 1 ? (384 / NT) : 1; };
+template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = NT == 256 ? 2 : (384 / NT > 1 ? 384 / NT : 1); };
+template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = NT == 256 ? 2 : (384 / NT > 1 ? 384 / NT : 1); };
 
 // RK = true: the launch is Runge-Kutta stage `stage` (1 or 2) of every mesh
 // (hydro_tile); the first stage leaves dt as it is.
