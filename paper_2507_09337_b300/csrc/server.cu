@@ -106,23 +106,30 @@ struct Req {
     double* totals = nullptr;
     double* partial = nullptr;       // nblk x 5 doubles: per-block sums of the totals reduction
     int cur_host = 0, steps_left = 0, nitems = 0, err_slot = -1;
-    int tx = 8, ty = 8;              // column tile of the hydro launch this request joins
+    int kind = 0, tx = 8, ty = 8;    // tile kind and column tile of the hydro launch this request joins
     int prec = orcha::kF64;          // arithmetic variant of the hydro task (orcha::Prec)
     cudaEvent_t ev = nullptr;        // admission done / completion landed
     RS st = RS::Pending;
     orcha_request_stats stats{};
 };
 
-// One launch per (ndim 2 or 3) x (FP64, FP32 flux or FF) x (tile 8x8 or
-// 16x8): blocks of 16 or more cells across x use the 16x8 tile (the
-// autotuner's choice for 16^3 blocks on a B300), 8-cell blocks the 8x8 one.
+// One launch per (ndim 2 or 3) x (FP64, FP32 flux or FF) x tile kind (0: 8x8,
+// 1: 16x8, 2: 16x16): blocks 8 cells across x use the 8x8 tile; wider ones
+// the autotuner's choice for 16^3 blocks on a B300, 16x16 for FP64 and FF in
+// 3D when the blocks are 16 or more cells across y too, else 16x8.
 constexpr int kServePrec = 3;        // kF64, kF32, kFF (Runge-Kutta steps are not served)
-constexpr int kGroups = 2 * kServePrec * 2;
+constexpr int kTileKinds = 3;
+constexpr int kGroups = 2 * kServePrec * kTileKinds;
 __host__ __device__ constexpr int group_ndim(int g) { return 2 + (g & 1); }
 __host__ __device__ constexpr int group_prec(int g) { return (g >> 1) % kServePrec; }
-__host__ __device__ constexpr int group_tx(int g) { return (g >> 1) / kServePrec ? 16 : 8; }
-constexpr int group_of(int ndim, int prec, int tx) { return (ndim - 2) | ((prec + (tx == 16 ? kServePrec : 0)) << 1); }
-static_assert(group_of(group_ndim(11), group_prec(11), group_tx(11)) == 11, "group index round trip");
+__host__ __device__ constexpr int group_kind(int g) { return (g >> 1) / kServePrec; }
+__host__ __device__ constexpr int group_tx(int g) { return group_kind(g) >= 1 ? 16 : 8; }
+__host__ __device__ constexpr int group_ty(int g) { return group_kind(g) == 2 ? 16 : 8; }
+constexpr int group_of(int ndim, int prec, int kind) { return (ndim - 2) | ((prec + kind * kServePrec) << 1); }
+constexpr int tile_kind(int ndim, int prec, const int* bs) {
+    return bs[0] < 16 ? 0 : (ndim == 3 && prec != orcha::kF32 && bs[1] >= 16 ? 2 : 1);
+}
+static_assert(group_of(group_ndim(17), group_prec(17), group_kind(17)) == 17, "group index round trip");
 
 struct GroupBuf {                    // host/device work list of one launch
     std::vector<orcha::SlotDev> slots_h;
@@ -253,13 +260,13 @@ bool orcha_server::launch_step(bool* launched) {
     }
     std::vector<Req*> finished;
     for (int gi = 0; gi < kGroups; ++gi) {
-        const int ndim = group_ndim(gi), prec = group_prec(gi), gtx = group_tx(gi), gty = 8;
+        const int ndim = group_ndim(gi), prec = group_prec(gi), gtx = group_tx(gi), gty = group_ty(gi);
         GroupBuf& g = s.g[gi];
         g.slots_h.clear();
         g.items_h.clear();
         std::vector<Req*> grp;
         for (Req* r : active)
-            if (group_of(r->m.ndim, r->prec, r->tx) == gi) grp.push_back(r);
+            if (group_of(r->m.ndim, r->prec, r->kind) == gi) grp.push_back(r);
         if (grp.empty()) continue;
         for (size_t i = 0; i < grp.size(); ++i) {
             Req* r = grp[i];
@@ -435,9 +442,10 @@ orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, or
     for (int nd = 2; e == cudaSuccess && nd <= 3; ++nd) {
         e = orcha::configure_hydro(nd, 8, 8);
         if (e == cudaSuccess) e = orcha::configure_hydro(nd, 16, 8);
+        if (e == cudaSuccess) e = orcha::configure_hydro(nd, 16, 16);
     }
     for (int gi = 0; e == cudaSuccess && gi < kGroups; ++gi)
-        e = orcha::persistent_occupancy(group_ndim(gi), group_tx(gi), 8, group_prec(gi), &s->occ[gi]);
+        e = orcha::persistent_occupancy(group_ndim(gi), group_tx(gi), group_ty(gi), group_prec(gi), &s->occ[gi]);
     if (e != cudaSuccess) {
         orcha_status st = orcha::cuda_error(e, "server_create");
         s->stop = true;
@@ -518,8 +526,9 @@ orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, 
     r->bytes = 2 * round_up(r->state_elems * sizeof(double)) + round_up(r->nblk * sizeof(unsigned long long)) +
                5 * kAlign + round_up(r->nblk * 5 * sizeof(double));
     r->steps_left = rd->nsteps;
-    r->tx = rd->bs[0] >= 16 ? 16 : 8;
-    r->ty = 8;
+    r->kind = tile_kind(rd->ndim, r->prec, rd->bs);
+    r->tx = group_tx(group_of(rd->ndim, r->prec, r->kind));
+    r->ty = group_ty(group_of(rd->ndim, r->prec, r->kind));
     r->nitems = (int)r->nblk * (rd->bs[0] / r->tx) * (rd->bs[1] / r->ty);
     r->stats.zone_updates = (int64_t)r->nblk * r->ncell * rd->nsteps;
     if (r->bytes > s->pool.size) {
