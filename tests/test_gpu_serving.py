@@ -133,6 +133,31 @@ def test_served_request_matches_oracle_and_packet_path(oracle_mod):
     assert np.array_equal(G, P)
 
 
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_FF])
+def test_non_cubic_blocks_join_a_fitting_tile(oracle_mod, task):
+    """The server runs FP64 and FF requests whose blocks are 16 or more cells
+    across on 16x16 tiles; blocks 8 cells across y (16 x 8 x 16, 32 x 8 x 8)
+    join the 16x8 launch instead. Served together with a cubic request, each
+    result is within the FP64 parity rule of the oracle."""
+    reqs = []
+    for nb, bs in [((2, 3, 1), (16, 8, 16)), ((1, 2, 2), (32, 8, 8)), ((2, 1, 1), (16, 16, 16))]:
+        ncell = [nb[d] * bs[d] for d in range(3)]
+        L = max(ncell)
+        spec = wl.MeshSpec(ndim=3, nb=nb, bs=bs, hi=tuple(c / L for c in ncell))
+        g = spec.gamma
+        reqs.append(dict(spec=spec, kind=2, region=(0, ncell[0] // 2, 0, 0), u_in=tuple(wl._cons(g, 1.0, 1.0, 3)),
+                         u_out=tuple(wl._cons(g, 0.125, 0.1, 3)), nsteps=3))
+    outs, stats, _ = _serve(reqs, task=task)
+    for r, G, st in zip(reqs, outs, stats):
+        assert st.status == 0
+        spec = r["spec"]
+        U0 = wl.region_state(spec, 2, r["region"], r["u_in"], r["u_out"])
+        O, _ = oracle_steps(oracle_mod, spec, U0, 3)
+        e = rule12_error(G, O, spec.nvar)
+        print(f"served {spec.bs} task {task}: rule-12 error {e:.3e}")
+        assert e <= 1e-12
+
+
 def test_submit_validation_and_timeout():
     import torch
     srv = serve.Server(64 << 20)
