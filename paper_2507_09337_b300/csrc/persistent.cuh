@@ -70,8 +70,9 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // on a B300): the FP64 variant, bound by the FP64 pipe, gains from 384
 // threads per SM (a small spill; +2 %); the FP32-flux variant runs best at
 // 768 threads per SM for 16x8 and 16x16 tiles (80 registers, a 20-byte
-// spill: +4.8 % and +19 % over 640; six 16x8 CTAs is also what its shared
-// memory allows) and at 640 for 8x8 tiles (768 loses 12 %). The double-word
+// spill: +4.8 % and +19 % over 640; seven 16x8 CTAs would fit the shared
+// memory but at 72 registers spill and lose 10 %) and at 640 for 8x8 tiles
+// (768 loses 12 %). The double-word
 // variant has the FP64 variant's register and shared-memory footprint
 // (8-byte values) and takes its bound. Both run 16x16 tiles at two CTAs per
 // SM (128 registers, a ~100-byte spill; two 109 KB tiles fill the SM's
