@@ -1,13 +1,17 @@
 // common.cuh -- device-side types shared by the block-hydro kernels.
 //
 // Arithmetic contract of the FP64 path (type rd). Default build
-// (ORCHA_FP64_CONTRACT = 1): IEEE-754 double operations that the compiler may
-// contract into FMAs, plus two rewrites that need fewer FP64-pipe slots (the
-// HLL sound speed as x * rsqrt(x * rho), the predictor as an FMA chain); the
-// result differs from the unfused definition by rounding only (a few ulp
-// per step). Exact build (ORCHA_FP64_CONTRACT = 0): every operation is one
-// round-to-nearest operation, none fused or reordered, through the __d*_rn
-// intrinsics, so the kernels evaluate the definition's expression trees and
+// (ORCHA_FP64_CONTRACT = 1): a product a * b written directly as an operand
+// of a sum or difference is fused into it (one FMA, the product unrounded);
+// every other operation is one round-to-nearest operation that the compiler
+// may not contract. Where products are fused is thus fixed by the source
+// expressions, so every kernel instantiation (tile shape, launch bounds,
+// packet or persistent path) gives the same bits. Two more rewrites need
+// fewer FP64-pipe slots (the HLL sound speed as x * rsqrt(x * rho), the
+// predictor as an FMA chain). The result differs from the unfused definition
+// by rounding only (a few ulp per step). Exact build (ORCHA_FP64_CONTRACT =
+// 0): every operation is one round-to-nearest operation, none fused or
+// reordered, so the kernels evaluate the definition's expression trees and
 // reproduce an unfused CPU evaluation of them bit for bit. The FP32 flux path
 // uses plain float, where contraction is allowed.
 #pragma once
@@ -19,20 +23,35 @@ namespace orcha {
 
 constexpr int kGuard = 2;   // guard layers per side: the scheme's stencil reaches two cells
 
-// ---------------------------------------------------------------- FP64, never fused
+// ---------------------------------------------------------------- FP64: fused only where written
+struct rdp;
 struct rd {
     double v;
     __device__ __forceinline__ rd() {}
     __device__ __forceinline__ constexpr rd(double x) : v(x) {}
+    __device__ __forceinline__ rd(const rdp& p);
 };
 #ifndef ORCHA_FP64_CONTRACT
 #define ORCHA_FP64_CONTRACT 1
 #endif
 constexpr bool kContract = ORCHA_FP64_CONTRACT != 0;
+// The product a * b not yet rounded (default build): a sum or difference that
+// takes it as an operand is one FMA; any other use rounds it first. With two
+// products as operands the left one is fused and the right one rounded.
+struct rdp {
+    double a, b;
+};
+__device__ __forceinline__ rd::rd(const rdp& p) { v = __dmul_rn(p.a, p.b); }
 #if ORCHA_FP64_CONTRACT
-__device__ __forceinline__ rd operator+(rd a, rd b) { return rd(a.v + b.v); }
-__device__ __forceinline__ rd operator-(rd a, rd b) { return rd(a.v - b.v); }
-__device__ __forceinline__ rd operator*(rd a, rd b) { return rd(a.v * b.v); }
+__device__ __forceinline__ rd operator+(rd a, rd b) { return rd(__dadd_rn(a.v, b.v)); }
+__device__ __forceinline__ rd operator-(rd a, rd b) { return rd(__dsub_rn(a.v, b.v)); }
+__device__ __forceinline__ rdp operator*(rd a, rd b) { return rdp{a.v, b.v}; }
+__device__ __forceinline__ rd operator+(rdp p, rd c) { return rd(fma(p.a, p.b, c.v)); }
+__device__ __forceinline__ rd operator+(rd c, rdp p) { return rd(fma(p.a, p.b, c.v)); }
+__device__ __forceinline__ rd operator-(rdp p, rd c) { return rd(fma(p.a, p.b, -c.v)); }
+__device__ __forceinline__ rd operator-(rd c, rdp p) { return rd(fma(-p.a, p.b, c.v)); }
+__device__ __forceinline__ rd operator+(rdp p, rdp q) { return rd(fma(p.a, p.b, __dmul_rn(q.a, q.b))); }
+__device__ __forceinline__ rd operator-(rdp p, rdp q) { return rd(fma(p.a, p.b, -__dmul_rn(q.a, q.b))); }
 #else
 __device__ __forceinline__ rd operator+(rd a, rd b) { return rd(__dadd_rn(a.v, b.v)); }
 __device__ __forceinline__ rd operator-(rd a, rd b) { return rd(__dsub_rn(a.v, b.v)); }
@@ -69,9 +88,10 @@ template <> struct P<rd> {
     static __device__ __forceinline__ rd sqrt(rd x) { return rd(__dsqrt_rn(x.v)); }
     // sqrt(x / rho) for x = gamma * p: the definition's sqrt(x * (1/rho)), or in
     // the contracted build x * rsqrt(x * rho) (one reciprocal square root
-    // instead of a reciprocal and a square root; rsqrt is within 1 ulp).
-    static __device__ __forceinline__ rd sound(rd x, rd rho) {
-        if constexpr (kContract) return rd(x.v * ::rsqrt(x.v * rho.v));
+    // instead of a reciprocal and a square root; rsqrt is within 1 ulp), left
+    // as an unrounded product so that each wave speed u -+ c is one FMA.
+    static __device__ __forceinline__ auto sound(rd x, rd rho) {
+        if constexpr (kContract) return rdp{x.v, ::rsqrt(__dmul_rn(x.v, rho.v))};
         else return rd(__dsqrt_rn(__dmul_rn(x.v, __drcp_rn(rho.v))));
     }
     static __device__ __forceinline__ rd ld(const double* p) { return rd(*p); }

@@ -132,8 +132,8 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
     using AS = Arith<T, 32>;     // wave speeds
     using AC = Arith<T, 16>;     // combination
     const AS gs = as<AS>(g);
-    const AS cL = P<AS>::sound(gs * as<AS>(L[NV - 1]), as<AS>(L[0]));
-    const AS cR = P<AS>::sound(gs * as<AS>(R[NV - 1]), as<AS>(R[0]));
+    const auto cL = P<AS>::sound(gs * as<AS>(L[NV - 1]), as<AS>(L[0]));
+    const auto cR = P<AS>::sound(gs * as<AS>(R[NV - 1]), as<AS>(R[0]));
     AS a = as<AS>(L[1]) - cL, b = as<AS>(R[1]) - cR;
     const AS SL = P<AS>::lt(a, b) ? a : b;
     a = as<AS>(L[1]) + cL;
@@ -259,10 +259,20 @@ template <int NDIM, int TX, int TY>
 struct Tile {
     static constexpr int NV = NDIM + 2;
     static constexpr int NW = NV + 1;                 // primitives + 1/rho
-    static constexpr int NT = TX * TY;                // threads = interior columns
+    static constexpr int NT = TX * TY;                // owner threads = interior columns
     static constexpr int R2X = TX + 4, R2Y = TY + 4, R2N = R2X * R2Y;
     static constexpr int R1X = TX + 2, R1Y = TY + 2, R1N = R1X * R1Y;
     static constexpr int NRING = 2 * (TX + TY);       // predicted ring cells (corners unused)
+    // Threads per CTA. The FP64 Hancock variant adds one thread per ring cell
+    // (in whole warps), so the ring is predicted alongside the interior
+    // instead of after it by the first NRING owners: measured on a B300, 16x16
+    // tiles +4 %. The FP32-flux, double-word and Runge-Kutta variants lose with
+    // it (less predictor work per cell, or fewer CTAs per SM) and keep one
+    // thread per interior column.
+    template <class T, bool RK>
+    static constexpr int nb() {
+        return std::is_same<T, rd>::value && !RK ? (NT + NRING + 31) / 32 * 32 : NT;
+    }
     static constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
     static constexpr int NSLOT = (NDIM == 3) ? 3 : 1;
     template <class S>
@@ -328,18 +338,26 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         hd[d] = P<T>::in(__dmul_rn(0.5, cd[d]));      // (dt/2) / dx_d
     }
 
-    // owner column of this thread
-    const int ti = tid % TX, tj = tid / TX;
+    // Threads 0 .. NT-1 own an interior column (its z state stays in their
+    // registers); the ring cells are predicted by threads NT .. NT+NRING-1
+    // when the variant has them (kSplit), else by owners 0 .. NRING-1 after
+    // their own cell; every thread loads planes and forms face fluxes.
+    constexpr int NB = Tl::template nb<T, RK>();
+    constexpr bool kSplit = NB > NT;
+    const bool owner = !kSplit || tid < NT;
+    const int ti = tid % TX, tj = tid / TX;         // owner column
     const int o2 = (tj + 2) * R2X + (ti + 2);       // in the R2 plane
     const int o1 = (tj + 1) * R1X + (ti + 1);       // in the R1 plane
-    // ring cell of this thread (tid < NRING): bottom row, top row, left column, right column
+    // ring cell of this thread: bottom row, top row, left column, right column
+    const int rt = kSplit ? tid - NT : tid;
+    const bool ringer = rt >= 0 && rt < Tl::NRING;
     int rc1 = 0, rc2 = 0, rface = 0;
-    if (tid < Tl::NRING) {
+    if (ringer) {
         int ci, cj;
-        if (tid < TX) { ci = tid + 1; cj = 0; rface = 3; }                      // row -1: needs y+
-        else if (tid < 2 * TX) { ci = tid - TX + 1; cj = TY + 1; rface = 2; }   // row TY: needs y-
-        else if (tid < 2 * TX + TY) { ci = 0; cj = tid - 2 * TX + 1; rface = 1; }       // col -1: x+
-        else { ci = TX + 1; cj = tid - 2 * TX - TY + 1; rface = 0; }            // col TX: x-
+        if (rt < TX) { ci = rt + 1; cj = 0; rface = 3; }                        // row -1: needs y+
+        else if (rt < 2 * TX) { ci = rt - TX + 1; cj = TY + 1; rface = 2; }     // row TY: needs y-
+        else if (rt < 2 * TX + TY) { ci = 0; cj = rt - 2 * TX + 1; rface = 1; }         // col -1: x+
+        else { ci = TX + 1; cj = rt - 2 * TX - TY + 1; rface = 0; }             // col TX: x-
         rc1 = cj * R1X + ci;
         rc2 = (cj + 1) * R2X + (ci + 1);
     }
@@ -357,7 +375,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     // row length are even), so with 16-byte aligned state buffers the address
     // is 16-byte aligned.
     constexpr int R2P = R2N / 2;
-    constexpr int KMAX = (R2P + NT - 1) / NT;
+    constexpr int KMAX = (R2P + NB - 1) / NB;
     int bxy[KMAX][2], oxy[KMAX][2];       // per cell of pair k: source block's (x, y) index; in-block column offset
     unsigned interior_mask = 0;           // bit 2k + e: cell e of pair k is an interior column of the tile
     unsigned contig_mask = 0;             // bit k: the sources of pair k are consecutive
@@ -365,7 +383,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     for (int k = 0; k < KMAX; ++k) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int c = 2 * (tid + k * NT) + e;
+            const int c = 2 * (tid + k * NB) + e;
             const int ci = c % R2X, cj = c / R2X;
             int sbx = bc[0], sby = bc[1], sx = x0 + ci, sy = y0 + cj;
             if (GATHER) {
@@ -421,7 +439,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         plane_z(pzi, zb, zc);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (tid + k * NT >= R2P) break;
+            if (tid + k * NB >= R2P) break;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 if (e == 1 && ((contig_mask >> k) & 1u)) break;     // same 16 bytes as cell 0
@@ -440,7 +458,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         const bool zin = pzi >= z0 && pzi < z1;        // planes this item owns: each cell checked once
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int q = tid + k * NT;
+            const int q = tid + k * NB;
             if (q >= R2P) break;
             double u[2][NV];
             const double* s0 = src_of(k, 0, zb, zc);
@@ -659,34 +677,64 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
         // ---- P: predict
         T zlo[NV], zhi[NV];
-        {
+        if constexpr (kSplit) {
+            // owners and ring threads run the one predictor call site, so a cell
+            // gets the same bits as owner in one tile and as ring cell in the
+            // next (the contracted FP64 build leaves multiply-add fusion to the
+            // compiler, which may fuse two inlined copies differently)
             T flo[3][NV], fhi[3][NV];
-            predict(p, o2, flo, fhi);
-            if (inner) {
+            if (owner || ringer) predict(p, owner ? o2 : rc2, flo, fhi);
+            if (owner) {
+                if (inner) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
+                        P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
+                        P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
+                        P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
+                    }
+                }
+                if (NDIM == 3) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
+                }
+            } else if (ringer && inner) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
-                    P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
-                    P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
-                    P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
+                    const T fs = rface == 0 ? flo[0][v] : rface == 1 ? fhi[0][v] : rface == 2 ? flo[1][v] : fhi[1][v];
+                    P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs);
                 }
             }
-            if (NDIM == 3) {
+        } else {
+            {
+                T flo[3][NV], fhi[3][NV];
+                predict(p, o2, flo, fhi);
+                if (inner) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
+                    for (int v = 0; v < NV; ++v) {
+                        P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
+                        P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
+                        P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
+                        P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
+                    }
+                }
+                if (NDIM == 3) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
+                }
             }
-        }
-        if (inner && tid < Tl::NRING) {
-            T fs[NV];
-            predict_face(p, rc2, rface, fs);
+            if (inner && ringer) {
+                T fs[NV];
+                predict_face(p, rc2, rface, fs);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs[v]);
+                for (int v = 0; v < NV; ++v) P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs[v]);
+            }
         }
         __syncthreads();
 
         // ---- F: x and y face fluxes of plane p
         if (inner) {
-            for (int f = tid; f < Tl::NXF + Tl::NYF; f += NT) {
+            for (int f = tid; f < Tl::NXF + Tl::NYF; f += NB) {
                 int iL, iR, fL, fR, nrm;
                 if (f < Tl::NXF) {
                     const int fi = f % (TX + 1), fj = f / (TX + 1);
@@ -725,7 +773,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             T Fz[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) Fz[v] = P<T>::zero();
-            if (p >= z0) {
+            if (owner && p >= z0) {
                 T L[NV], R[NV];
                 L[0] = zp_prev[0]; L[1] = zp_prev[3]; L[2] = zp_prev[1]; L[3] = zp_prev[2]; L[4] = zp_prev[4];
                 R[0] = zlo[0]; R[1] = zlo[3]; R[2] = zlo[1]; R[3] = zlo[2]; R[4] = zlo[4];
@@ -736,6 +784,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             if (p >= z0 + 1) {
                 // plane q of the column: block qb above blk, in-block plane ql
                 const int q = p - 1, qb = q / bz, ql = q - qb * bz;
+                if (owner) {
                 const long long gi = (long long)qb * nbxy * m.blk_stride +
                                      ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
                 rd Un[NV];
@@ -748,27 +797,29 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                         const dw tz = cdw[2] * (Fz[v] - Fz_prev[v]);
                         Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
                     } else {
-                        const rd tz = rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
-                        const rd acc = rd(acc_prev[v]) + tz;
+                        const rd acc = rd(acc_prev[v]) +
+                                       rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
                         Un[v] = rd(Ub[gi + v * vs]) - acc;
                     }
                     // Heun stage 2: the average with the step's initial state, in FP64
                     if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                if (!RK || stage == 2) {
-                    smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
-                    // leaving a block (or the item's range): raise its signal speed (CTA-uniform)
-                    if (q == z1 - 1 || ql == bz - 1) {
-                        cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
-                        smaxb = 0ull;
-                    }
+                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                }
+                // leaving a block (or the item's range): raise its signal speed
+                // (CTA-uniform: every thread takes part, non-owners with 0)
+                if ((!RK || stage == 2) && (q == z1 - 1 || ql == bz - 1)) {
+                    cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
+                    smaxb = 0ull;
                 }
             }
+            if (owner) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
+                for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
+            }
         }
-        if (inner) {
+        if (inner && owner) {
             // x then y flux differences of plane p
             // high x face of the cell at o1, low x face at o1 - 1; high y face at o1, low at o1 - R1X
 #pragma unroll
@@ -782,11 +833,11 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                     const dw ty = cdw[1] * (P<T>::ld(&sGy[v * R1N + o1]) - P<T>::ld(&sGy[v * R1N + o1 - R1X]));
                     acc_dw[v] = tx + ty;
                 } else {
-                    const rd tx = rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1]))) -
-                                               rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1 - 1]))));
-                    const rd ty = rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1]))) -
-                                               rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1 - R1X]))));
-                    acc_prev[v] = (tx + ty).v;
+                    acc_prev[v] = (rd(cd[0]) * (rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1]))) -
+                                                rd(P<T>::to_double(P<T>::ld(&sGx[v * R1N + o1 - 1])))) +
+                                   rd(cd[1]) * (rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1]))) -
+                                                rd(P<T>::to_double(P<T>::ld(&sGy[v * R1N + o1 - R1X])))))
+                                      .v;
                 }
             }
             if (NDIM == 2) {
@@ -812,7 +863,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 // Packet path: one CTA per (packet block, column tile); guards come from the
 // padded block.
 template <int NDIM, int TX, int TY, class T, bool RK = false>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<T, RK>())
 hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
              const double* __restrict__ Uin, double* __restrict__ Uout, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

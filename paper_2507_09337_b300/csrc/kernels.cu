@@ -414,7 +414,7 @@ static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
     auto kern = hydro_kernel<NDIM, TX, TY, T, RK>;
     const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
-    kern<<<dim3((unsigned)(n * tx * ty)), dim3(TX * TY), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage);
+    kern<<<dim3((unsigned)(n * tx * ty)), dim3(Tl::template nb<T, RK>()), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage);
     return cudaGetLastError();
 }
 
@@ -434,7 +434,7 @@ static cudaError_t launch_persistent_t(const SlotDev* slots, const Item* items, 
                                        int stage, cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    persistent_kernel<NDIM, TX, TY, T, RK><<<grid, TX * TY, smem, st>>>(slots, items, nitems, queue, stage);
+    persistent_kernel<NDIM, TX, TY, T, RK><<<grid, Tl::template nb<T, RK>(), smem, st>>>(slots, items, nitems, queue, stage);
     return cudaGetLastError();
 }
 
@@ -442,7 +442,7 @@ template <int NDIM, int TX, int TY, class T, bool RK>
 static cudaError_t occupancy_t(int* per_sm) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T, RK>, TX * TY,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T, RK>, Tl::template nb<T, RK>(),
                                                          smem);
 }
 

@@ -78,14 +78,19 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // SM (128 registers, a ~100-byte spill; two 109 KB tiles fill the SM's
 // shared memory): FP64 +8 % and FF +27 % over one CTA, which makes 16x16
 // their fastest tile (FP64 +2.2 %, FF +9 % over 16x8).
-template <class T, int NT> struct MinBlocks { static constexpr int value = NT <= 64 ? 640 / NT : 768 / NT; };
-template <int NT> struct MinBlocks<rd, NT> { static constexpr int value = NT == 256 ? 2 : (384 / NT > 1 ? 384 / NT : 1); };
-template <int NT> struct MinBlocks<dw, NT> { static constexpr int value = NT == 256 ? 2 : (384 / NT > 1 ? 384 / NT : 1); };
+template <class T, int NB> struct MinBlocks { static constexpr int value = NB <= 64 ? 640 / NB : 768 / NB; };
+template <int NB> struct MinBlocks<rd, NB> {
+    static constexpr int value = NB == 256 ? 2 : (384 / NB > 1 ? 384 / NB : 1);
+};
+template <int NB> struct MinBlocks<dw, NB> {
+    static constexpr int value = NB == 256 ? 2 : (384 / NB > 1 ? 384 / NB : 1);
+};
 
 // RK = true: the launch is Runge-Kutta stage `stage` (1 or 2) of every mesh
 // (hydro_tile); the first stage leaves dt as it is.
 template <int NDIM, int TX, int TY, class T, bool RK = false>
-__global__ void __launch_bounds__(TX * TY, (MinBlocks<T, TX * TY>::value))
+__global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<T, RK>(),
+                                  (MinBlocks<T, Tile<NDIM, TX, TY>::template nb<T, RK>()>::value))
 persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ items, int nitems,
                   unsigned int* __restrict__ queue, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
