@@ -67,19 +67,26 @@ def kernel_source_hash() -> str:
 
 def profiled_traffic(profile_md: str, kernel: str):
     """DRAM bytes per launch from a committed ncu summary, or None if the
-    summary covers another kernel variant or the kernel code changed since
-    that capture (hash mismatch)."""
+    summary covers no capture of this kernel variant or the kernel code
+    changed since the captures (hash mismatch). The summary's indented
+    machine-readable lines hold one kernel_source_sha256 and one or more
+    `kernel:` lines, each followed by its traffic_bytes_per_launch."""
     path = os.path.join(ROOT, "profiles", profile_md)
     if not os.path.exists(path):
         return None
-    fields = {}
+    sha, traffic, current = None, {}, None
     for line in open(path):
         if ":" in line and line.startswith("    "):
-            k, v = line.strip().split(":", 1)
-            fields[k.strip()] = v.strip()
-    if fields.get("kernel_source_sha256") != kernel_source_hash() or fields.get("kernel") != kernel:
+            k, v = (t.strip() for t in line.strip().split(":", 1))
+            if k == "kernel_source_sha256":
+                sha = v
+            elif k == "kernel":
+                current = v
+            elif k == "traffic_bytes_per_launch" and current is not None:
+                traffic[current] = float(v)
+    if sha != kernel_source_hash():
         return None
-    return float(fields["traffic_bytes_per_launch"])
+    return traffic.get(kernel)
 
 
 def parse():
@@ -91,6 +98,8 @@ def parse():
     ap.add_argument("--workload", default="sedov128",
                     choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff",
                              "sedov128_rk2", "sedov128_rk2_f32", "sedov128_rk2_ff"])
+    ap.add_argument("--tile", default="", choices=["", "8x8", "16x8", "16x16"],
+                    help="column tile of the hydro kernel (default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-threads", type=int, default=0,
@@ -290,8 +299,13 @@ def main():
     stream.wait_stream(torch.cuda.current_stream(dev))   # buffers were set up on the current stream
     npk = len(mesh.packets)
     h = mesh.handle
-    # tile shape picked by the autotuner (cached per GPU and geometry; outside the timed region)
-    tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
+    # tile shape picked by the autotuner (cached per GPU and geometry; outside
+    # the timed region), or the one --tile names
+    if args.tile:
+        tx, ty = (int(v) for v in args.tile.split("x"))
+        tile = (tx, ty, float("nan"))
+    else:
+        tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
     batch = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
     hydro_events = []
     # per bench step: pack, signal speed (one launch), dt reduce, nt persistent launches, unpack
@@ -442,7 +456,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[task_name], "data": "synthetic",
         "config": {"workload": desc, "task": task_name, "zones_per_step": spec.zones * nt,
-                   "tile": f"{tile[0]}x{tile[1]} (autotuned, {tile[2]:.3f} ms/step on the tuning mesh)",
+                   "tile": (f"{tile[0]}x{tile[1]} (--tile)" if args.tile else
+                            f"{tile[0]}x{tile[1]} (autotuned, {tile[2]:.3f} ms/step on the tuning mesh)"),
                    "l2": "inputs larger than L2 (two 164 MB state buffers + 84 MB initial state)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "hydro_share_of_step": hydro_share,

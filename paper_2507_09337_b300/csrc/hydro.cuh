@@ -266,7 +266,7 @@ struct Tile {
     // Threads per CTA. The FP64 Hancock variant adds one thread per ring cell
     // (in whole warps), so the ring is predicted alongside the interior
     // instead of after it by the first NRING owners: measured on a B300, 16x16
-    // tiles +4 %. The FP32-flux, double-word and Runge-Kutta variants lose with
+    // tiles +5 %. The FP32-flux, double-word and Runge-Kutta variants lose with
     // it (less predictor work per cell, or fewer CTAs per SM) and keep one
     // thread per interior column.
     template <class T, bool RK>
@@ -677,58 +677,31 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
         // ---- P: predict
         T zlo[NV], zhi[NV];
-        if constexpr (kSplit) {
-            // owners and ring threads run the one predictor call site, so a cell
-            // gets the same bits as owner in one tile and as ring cell in the
-            // next (the contracted FP64 build leaves multiply-add fusion to the
-            // compiler, which may fuse two inlined copies differently)
+        if (owner) {
             T flo[3][NV], fhi[3][NV];
-            if (owner || ringer) predict(p, owner ? o2 : rc2, flo, fhi);
-            if (owner) {
-                if (inner) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
-                        P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
-                        P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
-                        P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
-                    }
-                }
-                if (NDIM == 3) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
-                }
-            } else if (ringer && inner) {
+            predict(p, o2, flo, fhi);
+            if (inner) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const T fs = rface == 0 ? flo[0][v] : rface == 1 ? fhi[0][v] : rface == 2 ? flo[1][v] : fhi[1][v];
-                    P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs);
+                    P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
+                    P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
+                    P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
+                    P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
                 }
             }
-        } else {
-            {
-                T flo[3][NV], fhi[3][NV];
-                predict(p, o2, flo, fhi);
-                if (inner) {
+            if (NDIM == 3) {
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
-                        P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
-                        P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
-                        P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
-                    }
-                }
-                if (NDIM == 3) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
-                }
+                for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
             }
-            if (inner && ringer) {
-                T fs[NV];
-                predict_face(p, rc2, rface, fs);
+        }
+        // ring cells: the one face state the tile reads, the same bits as the
+        // owner of that cell forms (the FP64 operations and their fusion are
+        // fixed by the source, so both evaluations agree)
+        if (inner && ringer) {
+            T fs[NV];
+            predict_face(p, rc2, rface, fs);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs[v]);
-            }
+            for (int v = 0; v < NV; ++v) P<T>::st(&sFS[(rface * NV + v) * R1N + rc1], fs[v]);
         }
         __syncthreads();
 

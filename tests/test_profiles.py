@@ -1,0 +1,36 @@
+"""The committed ncu summaries under profiles/ against the kernel sources:
+bench.py reports a kernel's DRAM traffic from them only while the code they
+were captured on is unchanged, so a summary whose hash is stale would leave
+the bench line's roofline.traffic empty."""
+import os
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# summary -> kernel variants bench.py may time on that workload
+CAPTURED = {
+    "persistent_kernel_fp64_sedov128.md": ["persistent_kernel<3,16,16,rd>"],
+    "persistent_kernel_f32flux_sedov128.md": ["persistent_kernel<3,16,8,float>", "persistent_kernel<3,16,16,float>"],
+    "persistent_kernel_ff_sedov128.md": ["persistent_kernel<3,16,16,dw>"],
+}
+
+
+@pytest.mark.parametrize("md", sorted(CAPTURED))
+def test_summary_matches_current_kernel_code(md):
+    for kernel in CAPTURED[md]:
+        t = bench.profiled_traffic(md, kernel)
+        assert t is not None and t > 0, (md, kernel)
+    assert bench.profiled_traffic(md, "persistent_kernel<3,8,8,rd>") is None
+
+
+def test_stale_hash_gives_no_traffic(tmp_path, monkeypatch):
+    text = open(os.path.join(ROOT, "profiles", "persistent_kernel_fp64_sedov128.md")).read()
+    current = bench.kernel_source_hash()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "x.md").write_text(text.replace(current, "0" * 64))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: current)
+    assert bench.profiled_traffic("x.md", "persistent_kernel<3,16,16,rd>") is None
