@@ -15,7 +15,10 @@ import numpy as np
 from . import workloads as wl
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liborcha.so")
+# ORCHA_LIBRARY_VARIANT=exact loads liborcha_exact.so, the build in which every
+# FP64 operation is one unfused round-to-nearest operation
+LIB_PATH = os.path.join(HERE, {"": "liborcha.so", "default": "liborcha.so",
+                               "exact": "liborcha_exact.so"}[os.environ.get("ORCHA_LIBRARY_VARIANT", "")])
 
 ORCHA_OK = 0
 ORCHA_ERR_INVALID = -1
@@ -150,7 +153,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_09337_b300.build`")
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_09337_b300.build`"
+                              + (" --exact" if LIB_PATH.endswith("_exact.so") else ""))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)

@@ -1,9 +1,12 @@
 """Build the C-ABI library liborcha.so (CUDA for sm_103a) in the package directory.
 
-    python -m paper_2507_09337_b300.build [--force] [--verbose]
+    python -m paper_2507_09337_b300.build [--force] [--verbose] [--exact]
 
 The library is compiled with nvcc directly (no JIT cache), so the built file
-sits in-tree next to this script.
+sits in-tree next to this script. --exact builds liborcha_exact.so instead:
+the same sources with ORCHA_FP64_CONTRACT=0, where every FP64 operation is
+one unfused round-to-nearest operation (loaded by the binding when
+ORCHA_LIBRARY_VARIANT=exact).
 """
 from __future__ import annotations
 
@@ -15,6 +18,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liborcha.so")
+# library variant -> (file, extra nvcc flags)
+VARIANTS = {"default": ("liborcha.so", []),
+            "exact": ("liborcha_exact.so", ["-DORCHA_FP64_CONTRACT=0"])}
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,18 +37,24 @@ def _deps():
         [os.path.join(INCLUDE, "orcha.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(variant: str = "default") -> str:
+    return os.path.join(HERE, VARIANTS[variant][0])
+
+
+def up_to_date(variant: str = "default") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, variant: str = "default") -> str:
+    lib = lib_path(variant)
+    if not force and up_to_date(variant):
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, *NVFLAGS, f"-I{INCLUDE}", *sources(), "-o", LIB + ".tmp"]
+    cmd = [nvcc, *ARCH, *NVFLAGS, *VARIANTS[variant][1], f"-I{INCLUDE}", *sources(), "-o", lib + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -50,9 +62,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
     if verbose:
         sys.stderr.write(r.stdout + r.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                variant="exact" if "--exact" in sys.argv else "default"))

@@ -1,0 +1,44 @@
+"""Child process of tests/test_gpu_exact_build.py: runs the parity cases with
+the exact-FP64 library (ORCHA_LIBRARY_VARIANT=exact, set by the parent) and
+prints one JSON line per case comparing it with the oracle bit for bit."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2507_09337_b300 import binding as B  # noqa: E402
+from paper_2507_09337_b300 import workloads as wl  # noqa: E402
+from tests.gpu_helpers import gpu_batch_steps, gpu_steps, oracle_steps  # noqa: E402
+
+
+def main():
+    assert B.LIB_PATH.endswith("liborcha_exact.so"), B.LIB_PATH
+    spec2 = wl.sod_spec(64, 8)
+    sedov, packets = wl.sedov128_packets(64)
+    jumps = wl.MeshSpec(ndim=3, nb=(2, 2, 2), bs=(16, 16, 16), periodic=(1, 0, 1))
+    cases = [("sod64", spec2, wl.sod_state(spec2), None, 20, False, [(8, 8)]),
+             ("sedov128", sedov, wl.sedov_state(sedov), packets, 10, False, [(16, 16)]),
+             ("jumps", jumps, wl.random_blocky_state(jumps, 17), None, 4, False, [(8, 8), (16, 8), (16, 16)]),
+             ("sod64_rk2", spec2, wl.sod_state(spec2), None, 20, True, [(8, 8)])]
+    for name, spec, U0, pk, n, rk2, tiles in cases:
+        O, odts = oracle_steps(oracle, spec, U0, n, rk2=rk2)
+        task = B.ORCHA_TASK_HYDRO_RK2 if rk2 else B.ORCHA_TASK_HYDRO_FP64
+        res = {"case": name, "steps": n}
+        if not rk2:
+            G, gdts, err = gpu_steps(spec, U0, n, task=task, packets=pk, record_dt=True)
+            res["packet_path_bitwise"] = bool(np.array_equal(G, O)) and err == 0
+            res["dt_bitwise"] = bool(np.array_equal(gdts, odts))
+        for tile in tiles:
+            (H,), errs = gpu_batch_steps([(spec, U0, pk)], n, task=task, tile=tile)
+            res[f"batch_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(H, O)) and errs == [0]
+            res[f"batch_{tile[0]}x{tile[1]}_max_abs_diff"] = float(np.abs(H - O).max())
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

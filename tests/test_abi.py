@@ -46,6 +46,16 @@ def test_only_the_abi_is_exported(L):
     assert {s for s in syms if s.startswith("orcha_")} == set(declared_functions())
 
 
+def test_exact_build_exports_the_same_abi():
+    """The exact-FP64 library variant (every FP64 operation unfused) is the
+    same C ABI."""
+    import subprocess
+    path = pkgbuild.build(variant="exact")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {s for s in syms if s.startswith("orcha_")} == set(declared_functions())
+
+
 def _desc(**kw):
     d = B.orcha_mesh_desc()
     d.ndim = kw.get("ndim", 3)
