@@ -74,10 +74,14 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // memory but at 72 registers spill and lose 10 %) and at 640 for 8x8 tiles
 // (768 loses 12 %). The double-word
 // variant has the FP64 variant's register and shared-memory footprint
-// (8-byte values) and takes its bound. Both run 16x16 tiles at two CTAs per
-// SM (128 registers, a ~100-byte spill; two 109 KB tiles fill the SM's
-// shared memory): FP64 +8 % and FF +27 % over one CTA, which makes 16x16
-// their fastest tile (FP64 +2.2 %, FF +9 % over 16x8).
+// (8-byte values) and takes its bound. With one thread per interior column
+// both run 16x16 tiles at two 256-thread CTAs per SM (128 registers, a
+// ~100-byte spill; two 109 KB tiles fill the SM's shared memory): FP64 +8 %
+// and FF +27 % over one CTA, which made 16x16 their fastest tile (FP64
+// +2.2 %, FF +9 % over 16x8); the double-word and the FP64 Runge-Kutta
+// variants still run so. The FP64 Hancock variant adds ring threads (320
+// per 16x16 CTA): one CTA per SM, 162 registers, no spill, 5 % faster than
+// two 256-thread CTAs.
 template <class T, int NB> struct MinBlocks { static constexpr int value = NB <= 64 ? 640 / NB : 768 / NB; };
 template <int NB> struct MinBlocks<rd, NB> {
     static constexpr int value = NB == 256 ? 2 : (384 / NB > 1 ? 384 / NB : 1);
