@@ -758,27 +758,27 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                 // plane q of the column: block qb above blk, in-block plane ql
                 const int q = p - 1, qb = q / bz, ql = q - qb * bz;
                 if (owner) {
-                const long long gi = (long long)qb * nbxy * m.blk_stride +
-                                     ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
-                rd Un[NV];
+                    const long long gi = (long long)qb * nbxy * m.blk_stride +
+                                         ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                    rd Un[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    if constexpr (F32) {
-                        const ff tz = ff_scale(ff_diff(Fz[v], Fz_prev[v]), ch[2], cl[2]);
-                        Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
-                    } else if constexpr (DW) {
-                        const dw tz = cdw[2] * (Fz[v] - Fz_prev[v]);
-                        Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
-                    } else {
-                        const rd acc = rd(acc_prev[v]) +
-                                       rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
-                        Un[v] = rd(Ub[gi + v * vs]) - acc;
+                    for (int v = 0; v < NV; ++v) {
+                        if constexpr (F32) {
+                            const ff tz = ff_scale(ff_diff(Fz[v], Fz_prev[v]), ch[2], cl[2]);
+                            Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
+                        } else if constexpr (DW) {
+                            const dw tz = cdw[2] * (Fz[v] - Fz_prev[v]);
+                            Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
+                        } else {
+                            const rd acc = rd(acc_prev[v]) +
+                                           rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
+                            Un[v] = rd(Ub[gi + v * vs]) - acc;
+                        }
+                        // Heun stage 2: the average with the step's initial state, in FP64
+                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
+                        Ob[gi + v * vs] = Un[v].v;
                     }
-                    // Heun stage 2: the average with the step's initial state, in FP64
-                    if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
-                    Ob[gi + v * vs] = Un[v].v;
-                }
-                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                    if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
                 }
                 // leaving a block (or the item's range): raise its signal speed
                 // (CTA-uniform: every thread takes part, non-owners with 0)
