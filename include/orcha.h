@@ -88,7 +88,12 @@ typedef enum {
     /* One MUSCL-Hancock/HLL step of every packet block in FP64: reads the
      * current buffer (guards filled) and the device dt, writes the interiors
      * of the other buffer and the blocks' largest signal speed
-     * sum_d (|u_d| + c) / dx_d of the new state. */
+     * sum_d (|u_d| + c) / dx_d of the new state. The default library fuses a
+     * product into the sum or difference the scheme writes it in (one FMA)
+     * and rounds every other operation as written, so every tile shape and
+     * both the packet and the persistent path give the same bits; the
+     * library built with ORCHA_FP64_CONTRACT=0 (liborcha_exact.so) fuses
+     * nothing and reproduces an unfused FP64 evaluation bit for bit. */
     ORCHA_TASK_HYDRO_FP64 = 1,
     /* As HYDRO_FP64 with reconstruction, predictor and HLL fluxes in FP32
      * (from the FP64 state rounded to nearest); each face flux is promoted to
