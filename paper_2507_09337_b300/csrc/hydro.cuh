@@ -48,8 +48,9 @@ namespace orcha {
 #define ORCHA_EMU 0
 #endif
 // Whether a variant asks L2 for each plane's source lines two planes ahead of
-// its load. Measured on a B300 (128^3 Sedov): FF +7 %, FP64 neutral, FP32
-// flux -4 %, so only the FF variant does.
+// its load. Measured on a B300 (128^3 Sedov): FF +7 %, FP64 neutral (-0.4 %
+// with ring threads, one CTA per SM), FP32 flux -4 %, so only the FF variant
+// does.
 template <class T> struct Prefetch { static constexpr bool value = false; };
 template <> struct Prefetch<dw> { static constexpr bool value = true; };
 
