@@ -523,7 +523,6 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         using A = A2;
         const int sc = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
         const S* w = sW + sc * NW * R2N;
-        A a[3][NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) Wc[v] = as<A>(P<T>::ld(&w[v * R2N + c2]));
         const A rc = as<A>(P<T>::ld(&w[NV * R2N + c2]));
@@ -551,23 +550,42 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             return;
         }
         const A gp = as<A>(g) * Wc[NV - 1];
+        if constexpr (kContract && std::is_same<A, rd>::value) {
+            // Wc - sum_d hd_d A_d dW_d regrouped: every row has the advective
+            // term sum_d (hd_d u_d) dW_d[v]; the density and pressure rows share
+            // the divergence D = sum_d hd_d du_d (times rho, gamma p); velocity
+            // row d adds hd_d dp_d / rho. 30 FP64 operations per 3D cell
+            // instead of the definition's 40; the same value up to rounding.
+            rd t[NDIM];
+            rd D = hd[0] * dW[0][1];
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            const A un = Wc[1 + d], dun = dW[d][1 + d], dp = dW[d][NV - 1];
-            a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);
+            for (int d = 0; d < NDIM; ++d) {
+                t[d] = hd[d] * Wc[1 + d];
+                if (d > 0) D = D + hd[d] * dW[d][1 + d];
+            }
 #pragma unroll
-            for (int t = 0; t < NDIM; ++t)
-                a[d][1 + t] = (t == d) ? ((un * dun) + (dp * rc)) : (un * dW[d][1 + t]);
-            a[d][NV - 1] = (gp * dun) + (un * dp);
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            if constexpr (kContract && std::is_same<A, rd>::value) {
-                // Wc - sum_d hd_d a_d as a chain of fused multiply-subtracts
+            for (int v = 0; v < NV; ++v) {
                 Wb[v] = Wc[v];
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) Wb[v] = rd(fma(-hd[d].v, a[d][v].v, Wb[v].v));
-            } else {
+                for (int d = 0; d < NDIM; ++d) Wb[v] = Wb[v] - t[d] * dW[d][v];
+            }
+            Wb[0] = Wb[0] - Wc[0] * D;
+            Wb[NV - 1] = Wb[NV - 1] - gp * D;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) Wb[1 + d] = Wb[1 + d] - rc * rd(hd[d] * dW[d][NV - 1]);
+        } else {
+            A a[3][NV];
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                const A un = Wc[1 + d], dun = dW[d][1 + d], dp = dW[d][NV - 1];
+                a[d][0] = (un * dW[d][0]) + (Wc[0] * dun);
+#pragma unroll
+                for (int t = 0; t < NDIM; ++t)
+                    a[d][1 + t] = (t == d) ? ((un * dun) + (dp * rc)) : (un * dW[d][1 + t]);
+                a[d][NV - 1] = (gp * dun) + (un * dp);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
                 A s = as<A>(hd[0]) * a[0][v];
 #pragma unroll
                 for (int d = 1; d < NDIM; ++d) s = s + (as<A>(hd[d]) * a[d][v]);
