@@ -550,18 +550,21 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             return;
         }
         const A gp = as<A>(g) * Wc[NV - 1];
-        if constexpr (kContract && std::is_same<A, rd>::value) {
+        // The exact FP64 build (and the software-FP64 type) evaluates the
+        // definition's expression tree; every other arithmetic the regrouped form.
+        constexpr bool kRegroup = std::is_same<A, rd>::value ? kContract : !std::is_same<A, re>::value;
+        if constexpr (kRegroup) {
             // Wc - sum_d hd_d A_d dW_d regrouped: every row has the advective
             // term sum_d (hd_d u_d) dW_d[v]; the density and pressure rows share
             // the divergence D = sum_d hd_d du_d (times rho, gamma p); velocity
-            // row d adds hd_d dp_d / rho. 30 FP64 operations per 3D cell
-            // instead of the definition's 40; the same value up to rounding.
-            rd t[NDIM];
-            rd D = hd[0] * dW[0][1];
+            // row d adds hd_d dp_d / rho. 30 operations per 3D cell instead of
+            // the definition's 40; the same value up to rounding.
+            A t[NDIM];
+            A D = as<A>(hd[0]) * dW[0][1];
 #pragma unroll
             for (int d = 0; d < NDIM; ++d) {
-                t[d] = hd[d] * Wc[1 + d];
-                if (d > 0) D = D + hd[d] * dW[d][1 + d];
+                t[d] = as<A>(hd[d]) * Wc[1 + d];
+                if (d > 0) D = D + as<A>(hd[d]) * dW[d][1 + d];
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -572,7 +575,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             Wb[0] = Wb[0] - Wc[0] * D;
             Wb[NV - 1] = Wb[NV - 1] - gp * D;
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d) Wb[1 + d] = Wb[1 + d] - rc * rd(hd[d] * dW[d][NV - 1]);
+            for (int d = 0; d < NDIM; ++d) Wb[1 + d] = Wb[1 + d] - rc * A(as<A>(hd[d]) * dW[d][NV - 1]);
         } else {
             A a[3][NV];
 #pragma unroll
