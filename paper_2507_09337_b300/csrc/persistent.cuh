@@ -80,7 +80,8 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
 // and FF +27 % over one CTA, which made 16x16 their fastest tile (FP64
 // +2.2 %, FF +9 % over 16x8); the double-word and the FP64 Runge-Kutta
 // variants still run so. The FP64 Hancock variant adds ring threads (320
-// per 16x16 CTA): one CTA per SM, 162 registers, no spill, 5 % faster than
+// per 16x16 CTA): one CTA per SM at up to 168 registers (three of its ten
+// warps share one of the SM's four 16 K-register files), 5 % faster than
 // two 256-thread CTAs.
 template <class T, int NB> struct MinBlocks { static constexpr int value = NB <= 64 ? 640 / NB : 768 / NB; };
 template <int NB> struct MinBlocks<rd, NB> {
