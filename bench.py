@@ -370,8 +370,10 @@ def main():
         flops = FLOPS_PER_ZONE_3D_RK2 if task_name == "rk2" else FLOPS_PER_ZONE_3D
         achieved = flops * zones_per_launch / avg_launch_s / 1e12
         kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
-        traffic = (profiled_traffic("persistent_kernel_fp64_sedov128.md", kname)
-                   if args.workload == "sedov128" else None)        # RK2: a step is two launches; not recorded
+        # RK2: the recorded traffic is per time step (its two stage launches)
+        prof = {"sedov128": "persistent_kernel_fp64_sedov128.md",
+                "sedov128_rk2": "persistent_kernel_rk2_sedov128.md"}.get(args.workload)
+        traffic = profiled_traffic(prof, kname) if prof else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": kname, "per_launch": "one time step of all packets" + (

@@ -15,6 +15,7 @@ CAPTURED = {
     "persistent_kernel_fp64_sedov128.md": ["persistent_kernel<3,16,16,rd>"],
     "persistent_kernel_f32flux_sedov128.md": ["persistent_kernel<3,16,8,float>", "persistent_kernel<3,16,16,float>"],
     "persistent_kernel_ff_sedov128.md": ["persistent_kernel<3,16,16,dw>"],
+    "persistent_kernel_rk2_sedov128.md": ["persistent_kernel<3,16,16,rd,true>"],
 }
 
 
