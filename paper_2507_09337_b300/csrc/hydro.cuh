@@ -11,16 +11,20 @@
 // "Experiments") describes the task only as explicit finite volume with
 // guard-cell halos refreshed before it runs; the expression trees below are
 // the ones of the FP64 definition, operation for operation (the contracted
-// FP64 build fuses multiply-adds and rewrites two of them; see common.cuh).
+// FP64 build fuses a product into the sum it is written in, and regroups the
+// predictor and rewrites the sound speed and the HLL combination; see
+// common.cuh).
 //
 // GPU mapping. One CTA owns a TX x TY column tile of one block and sweeps it
-// along z (2.5D blocking), one thread per interior column. Per plane:
+// along z (2.5D blocking), one owner thread per interior column (the FP64
+// Hancock variant adds one thread per tile-ring cell). Per plane:
 //   L  primitives of the (TX+4)(TY+4) plane two layers ahead into a ring of
 //      three planes in shared memory (the z stencil needs p-1, p, p+1), read
 //      as 16-byte pairs of x-neighbours;
 //   P  slopes, predictor and face states of plane p: interior cells by their
 //      owner thread (z face states stay in its registers), the one-cell ring
-//      around the tile by the first 2(TX+TY) threads (x/y face states only);
+//      around the tile by the ring threads, or else by the first 2(TX+TY)
+//      owners after their own cell (the one x or y face state a tile reads);
 //   F  every x and y face flux of plane p once, into shared memory over the
 //      face state it was formed from;
 //   U  each owner forms its z face flux from registers, finishes the update
