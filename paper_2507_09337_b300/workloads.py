@@ -399,3 +399,19 @@ def serving_stream(n: int, rate: float, seed_arrivals: int = 1, seed_requests: i
     rr = np.random.default_rng(seed_requests)
     t = np.cumsum(ra.exponential(1.0, size=n)) / rate
     return [(float(t[i]), serving_request(rr, **kw)) for i in range(n)]
+
+
+def ramp_state(spec: MeshSpec, var: str, delta: float = 0.1, u: float = 10.0, base: float = 1.0) -> np.ndarray:
+    """Uniform flow u along x with a linear ramp along x in one primitive:
+    var = "p": rho = base, p = delta (i + 1); var = "rho": p = base,
+    rho = delta (i + 1) (i the global x index); v = w = 0. Initial data of the
+    first-order fallback cases (a large time step drives the low end of the
+    ramp's Hancock face states negative)."""
+    x, y, z = spec.centers()
+    if spec.ndim == 2:
+        x = x[0]
+    ramp = np.broadcast_to(delta * (np.arange(spec.ncells[0]) + 1.0), x.shape)
+    flat = np.full(x.shape, base)
+    rho, p = (flat, ramp) if var == "p" else (ramp, flat)
+    vel = [np.full(x.shape, u)] + [np.zeros(x.shape)] * (spec.ndim - 1)
+    return to_blocks(spec, _globalize(spec, cons_from_prim_global(spec, rho, vel, p)))

@@ -2,9 +2,9 @@
 
 Each case copies oracle/oracle.c, replaces one expression with a plausible
 mistake (a dropped term, a wrong sign, a wrong index, a wrong constant, a
-wrong boundary rule), compiles the copy with the oracle's own flags, binds the
-oracle API to it, and runs the pin tests of tests/test_oracle_pins.py against
-it: at least one pin must fail. Mistakes are planted only in a temporary copy
+wrong boundary rule, a wrong first-order fallback rule), compiles the copy
+with the oracle's own flags, binds the oracle API to it, and runs the pin
+tests of tests/test_oracle_pins.py against it: at least one pin must fail. Mistakes are planted only in a temporary copy
 of the oracle, on the CPU.
 """
 import os
@@ -40,6 +40,21 @@ MUTATIONS = {
     "outflow_reflects_inner_cell": ("if (gi > n - 1) return n - 1;", "if (gi > n - 1) return n - 2;"),
     "periodic_off_by_one": ("if (periodic) { gi %= n; if (gi < 0) gi += n; return gi; }",
                             "if (periodic) { gi %= n; if (gi < 0) gi += n - 1; return gi; }"),
+    # the first-order fallback rule
+    "fallback_tests_rho_only": ("if (!(q[0] > 0.0) || !(q[nv - 1] > 0.0)) ok = 0;", "if (!(q[0] > 0.0)) ok = 0;"),
+    "fallback_tests_p_only": ("if (!(q[0] > 0.0) || !(q[nv - 1] > 0.0)) ok = 0;", "if (!(q[nv - 1] > 0.0)) ok = 0;"),
+    "fallback_reverts_offending_faces_only": (
+        """                        if (!(q[0] > 0.0) || !(q[nv - 1] > 0.0)) ok = 0;
+                    }
+                if (!ok) {""",
+        """                        if (!(q[0] > 0.0) || !(q[nv - 1] > 0.0)) {
+                            ok = 0;
+                            for (int v = 0; v < nv; ++v) ((double*)q)[v] = Wc[v];
+                        }
+                    }
+                if (0) {"""),
+    "fallback_to_half_step_state": ("for (int v = 0; v < nv; ++v) fs[(d * 2 + s) * MAXV + v] = Wc[v];",
+                                    "for (int v = 0; v < nv; ++v) fs[(d * 2 + s) * MAXV + v] = Wbar[v];"),
     # the Heun RK2 integrator
     "rk2_forward_euler_twice": ("Unew[o] = Ubase ? (0.5 * (Ubase[o] + us)) : us;", "Unew[o] = us;"),
     "rk2_stage_weights": ("(0.5 * (Ubase[o] + us))", "((0.25 * Ubase[o]) + (0.75 * us))"),
@@ -55,6 +70,8 @@ PIN_TESTS = [
     ("minmod", lambda o: pins.test_minmod_brute_force(o)),
     ("hll_identical", lambda o: pins.test_hll_identical_states_is_physical_flux(o)),
     ("hll_subsonic", lambda o: pins.test_hll_subsonic_against_hand_values(o)),
+    ("fallback_hand_p", lambda o: pins.test_first_order_fallback_hand_case(o, "p")),
+    ("fallback_hand_rho", lambda o: pins.test_first_order_fallback_hand_case(o, "rho")),
     ("dt_closed_form", lambda o: pins.test_dt_closed_form(o)),
     ("sod_exact", lambda o: pins.test_sod_2d_matches_exact_solution_and_rows_are_identical(o)),
     ("free_stream", lambda o: pins.test_free_stream_is_preserved_bitwise(o, 3, (0, 0, 0))),
