@@ -13,7 +13,7 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 from paper_2507_09337_b300 import binding as B  # noqa: E402
 from paper_2507_09337_b300 import workloads as wl  # noqa: E402
-from tests.gpu_helpers import gpu_batch_steps, gpu_steps, oracle_steps  # noqa: E402
+from tests.gpu_helpers import gpu_batch_steps, gpu_one_step, gpu_steps, oracle_steps  # noqa: E402
 
 
 def main():
@@ -37,6 +37,24 @@ def main():
             (H,), errs = gpu_batch_steps([(spec, U0, pk)], n, task=task, tile=tile)
             res[f"batch_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(H, O)) and errs == [0]
             res[f"batch_{tile[0]}x{tile[1]}_max_abs_diff"] = float(np.abs(H - O).max())
+        print(json.dumps(res), flush=True)
+    # the first-order fallback: one step at 40x the CFL time step of smeared
+    # random jumps, and the ramp hand case
+    oracle.set_threads(8)
+    m = oracle.Mesh(**jumps.oracle_kwargs())
+    U1, _, _ = oracle.run(m, wl.random_blocky_state(jumps, 21), 2)
+    dt = 40.0 * oracle.dt(m, U1)
+    ramp = wl.MeshSpec(ndim=2, nb=(2, 1, 1), bs=(16, 16, 1), periodic=(0, 1, 0))
+    cases = [("fallback40", jumps, U1, dt)]
+    for var in ("p", "rho"):
+        cases.append((f"fallback_ramp_{var}", ramp, wl.ramp_state(ramp, var, 0.1, 10.0), 0.85 * ramp.dx(0)))
+    for name, spec, U0, step_dt in cases:
+        O, _, nfirst = oracle.step(oracle.Mesh(**spec.oracle_kwargs()), U0, step_dt)
+        res = {"case": name, "nfirst": nfirst}
+        for tile in [(8, 8), (16, 8), (16, 16)]:
+            for path in ("packet", "batch"):
+                G = gpu_one_step(spec, U0, step_dt, B.ORCHA_TASK_HYDRO_FP64, tile, path)
+                res[f"{path}_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(G, O))
         print(json.dumps(res), flush=True)
 
 

@@ -6,11 +6,12 @@ from paper_2507_09337_b300 import binding as B
 from paper_2507_09337_b300 import workloads as wl
 
 
-def rule12_error(G: np.ndarray, O: np.ndarray, nvar: int) -> float:
+def rule12_error(G: np.ndarray, O: np.ndarray, nvar: int, extra_scale=None) -> float:
     """Largest |g - o| / max(|o|, s_v) over cells and variables, where s_v is the
     field's largest |momentum| for momentum components and |o| alone for rho
     and E (a plain relative error is meaningless where momentum is zero by
-    symmetry). Arrays are block arrays [block, var, ...]."""
+    symmetry). Arrays are block arrays [block, var, ...]. extra_scale (an
+    array of the same shape) joins the per-cell maximum when given."""
     G = np.asarray(G)
     O = np.asarray(O)
     err = 0.0
@@ -18,6 +19,8 @@ def rule12_error(G: np.ndarray, O: np.ndarray, nvar: int) -> float:
     for v in range(nvar):
         o, g = O[:, v], G[:, v]
         scale = np.abs(o)
+        if extra_scale is not None:
+            scale = np.maximum(scale, np.abs(np.asarray(extra_scale)[:, v]))
         if 0 < v < nvar - 1:
             scale = np.maximum(scale, mom)
         d = np.abs(g - o)
@@ -91,3 +94,47 @@ def gpu_batch_steps(problems, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, tile=(0, 0),
             B.orcha_batch_destroy(batch)
         for m in meshes:
             m.close()
+
+
+def _poll(mesh, stream=None):
+    try:
+        return mesh.poll(stream)
+    except B.OrchaError:
+        return -1
+
+
+def gpu_one_step(spec, U0, dt, task, tile, path):
+    """One step (or stage) of `task` at a time step the caller gives (written
+    into the mesh's dt_dev), through the packet path (guard fill + task, per
+    stage for HYDRO_RK2) or one persistent batch launch with init_dt = 0.
+    The device error word is read and cleared, not checked. Returns the new
+    state."""
+    import torch
+    mesh = B.Mesh(spec)
+    batch = None
+    try:
+        mesh.set_tile(*tile)
+        mesh.load(U0)
+        mesh.dt.fill_(dt)
+        if path == "packet":
+            if task == B.ORCHA_TASK_HYDRO_RK2:
+                for st in (B.ORCHA_TASK_RK2_STAGE1, B.ORCHA_TASK_RK2_STAGE2):
+                    mesh.run(B.ORCHA_TASK_GUARD_FILL)
+                    mesh.run(st)
+                    B.orcha_mesh_swap(mesh.handle)
+            else:
+                mesh.run(B.ORCHA_TASK_GUARD_FILL)
+                mesh.run(task)
+                B.orcha_mesh_swap(mesh.handle)
+            _poll(mesh)
+        else:
+            batch = B.orcha_batch_create(mesh.packets, *tile)
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            B.orcha_batch_advance(batch, task, 1, False, False, s)
+            _poll(mesh, s)
+        return mesh.store()
+    finally:
+        if batch:
+            B.orcha_batch_destroy(batch)
+        mesh.close()

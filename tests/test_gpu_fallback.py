@@ -1,0 +1,151 @@
+"""The first-order fallback on the GPU, against the oracle.
+
+At the CFL time step no cell of the parity workloads takes the fallback (the
+oracle counts 0 first-order cells on them), so these cases force it:
+
+* the hand case of tests/test_oracle_pins.py (a pressure or density ramp in
+  supersonic flow at half Courant number 4.25: three cells per row fall back,
+  one of them with only some faces non-positive), and
+* random jumps smeared by two steps, then one step at 40x the CFL time step
+  (the oracle reports well over 50 first-order cells).
+
+The caller owns dt_dev, so each case writes the time step into it and runs
+one guard fill + hydro task (packet path) or one persistent launch with
+init_dt = 0 (batch path), for every tile shape. FP64 and double-word tasks
+are held to the parity rule (|g - o| <= 1e-12 max(|o|, s_v)); the FP32-flux
+tasks (configured and shortcut update) report their relative L1(rho). The Runge-Kutta stages use the plain
+MUSCL operator, whose minmod face states lie between neighbouring values and
+never fall back (the oracle's count is 0 and the test asserts it); they are
+run at 4x the time step and held to the same rule. A 40x step leaves some
+cells non-physical, so the device error word is read and cleared but not
+required to be 0, and many new values are near-cancellations of terms tens of
+times larger: there the difference is scaled by the cell's old value too,
+and the double-word variant's per-term error is allowed to grow with the 40x
+step (tolerance 40 x 1e-12).
+The exact-FP64 library reproduces the oracle bit for bit on these cases
+(tests/test_gpu_exact_build.py).
+"""
+import numpy as np
+import pytest
+
+from paper_2507_09337_b300 import binding as B
+from paper_2507_09337_b300 import workloads as wl
+
+from .gpu_helpers import gpu_one_step, rule12_error
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+TILES = [(8, 8), (16, 8), (16, 16)]
+F32_TASKS = [B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_09337_b300 import build
+    build.build()
+
+
+def smeared_jumps(oracle_mod, periodic):
+    spec = wl.MeshSpec(ndim=3, nb=(2, 2, 2), bs=(16, 16, 16), periodic=periodic)
+    m = oracle_mod.Mesh(**spec.oracle_kwargs())
+    U0, _, _ = oracle_mod.run(m, wl.random_blocky_state(spec, 21), 2)
+    return spec, m, U0, 40.0 * oracle_mod.dt(m, U0)
+
+
+def term_scaled_error(G, O, U0, nvar):
+    """Largest |g - o| / max(|o|, |u0|, s_v): the parity rule with the cell's
+    old value in the scale. At 40x the CFL step the update's terms are tens of
+    times the state and many new values are their near-cancellation, where a
+    last-bit difference in a term is a large fraction of the result."""
+    return rule12_error(G, O, nvar, extra_scale=U0)
+
+
+def l1_rho(G, O):
+    return float(np.abs(G[:, 0] - O[:, 0]).sum() / np.abs(O[:, 0]).sum())
+
+
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_FF])
+@pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1)])
+def test_fallback_at_40x_dt_every_tile_and_path(oracle_mod, task, periodic):
+    spec, m, U0, dt = smeared_jumps(oracle_mod, periodic)
+    O, _, nfirst = oracle_mod.step(m, U0, dt)
+    print(f"task {task} periodic {periodic}: oracle first-order cells nfirst = {nfirst}")
+    assert nfirst > 50
+    # double-word arithmetic errs per term (~2^-48 of it), and the step's
+    # terms grow with dt: its bound scales with the 40x step
+    tol = TOL * (40.0 if task == B.ORCHA_TASK_HYDRO_FF else 1.0)
+    outs = []
+    for tile in TILES:
+        for path in ("packet", "batch"):
+            G = gpu_one_step(spec, U0, dt, task, tile, path)
+            e = rule12_error(G, O, spec.nvar)
+            et = term_scaled_error(G, O, U0, spec.nvar)
+            print(f"  tile {tile} {path}: rule-12 error {e:.3e}, with the old value in the scale {et:.3e}")
+            assert et <= tol
+            outs.append(G)
+    assert all(np.array_equal(outs[0], G) for G in outs[1:])
+
+
+@pytest.mark.parametrize("task", F32_TASKS)
+def test_fallback_at_40x_dt_f32flux(oracle_mod, task):
+    spec, m, U0, dt = smeared_jumps(oracle_mod, (0, 0, 0))
+    O, _, nfirst = oracle_mod.step(m, U0, dt)
+    outs = []
+    for tile in TILES:
+        for path in ("packet", "batch"):
+            G = gpu_one_step(spec, U0, dt, task, tile, path)
+            assert np.all(np.isfinite(G))
+            outs.append(G)
+    e = l1_rho(outs[0], O)
+    print(f"task {task} at 40x dt: nfirst = {nfirst}, relative L1(rho) to the FP64 oracle {e:.3e}")
+    assert e < 1e-4
+    assert all(np.array_equal(outs[0], G) for G in outs[1:])
+
+
+@pytest.mark.parametrize("var", ["p", "rho"])
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_FF] + F32_TASKS)
+def test_fallback_hand_case(oracle_mod, var, task):
+    """The oracle pin's ramp (three first-order cells per row, one of them
+    with non-positive faces on one side only), in 2D blocks of 16 x 16. The
+    large step leaves new values that cancel to ~0 (the density ramp's energy
+    at x cell 7 is 1e-13 from 0), so the old value joins the error scale."""
+    spec = wl.MeshSpec(ndim=2, nb=(2, 1, 1), bs=(16, 16, 1), periodic=(0, 1, 0))
+    u, K = 10.0, 4.25
+    U0 = wl.ramp_state(spec, var, 0.1, u)
+    dt = 2.0 * K * spec.dx(0) / u
+    O, _, nfirst = oracle_mod.step(oracle_mod.Mesh(**spec.oracle_kwargs()), U0, dt)
+    assert nfirst == 3 * spec.ncells[1]
+    for tile in TILES:
+        for path in ("packet", "batch"):
+            G = gpu_one_step(spec, U0, dt, task, tile, path)
+            if task in F32_TASKS:
+                e = l1_rho(G, O)
+                print(f"  {var} tile {tile} {path}: FP32-flux relative L1(rho) {e:.3e}")
+                assert e < 1e-6
+            else:
+                e = term_scaled_error(G, O, U0, spec.nvar)
+                print(f"  {var} tile {tile} {path}: error with the old value in the scale {e:.3e}")
+                assert e <= TOL
+
+
+def test_rk2_stages_at_4x_dt(oracle_mod):
+    """Stage 1 alone (packet task) and whole Heun steps (packet stages and the
+    persistent batch) at 4x the CFL time step (at 40x the first stage leaves
+    non-physical cells, which the second stage cannot take); the plain MUSCL
+    operator takes no fallback (oracle count 0)."""
+    spec, m, U0, dt = smeared_jumps(oracle_mod, (1, 0, 1))
+    dt = dt / 10.0
+    S1, _, nf1 = oracle_mod.stage(m, U0, dt)
+    O, _, nf = oracle_mod.step_rk2(m, U0, dt)
+    assert nf1 == 0 and nf == 0
+    for tile in TILES:
+        G1 = gpu_one_step(spec, U0, dt, B.ORCHA_TASK_RK2_STAGE1, tile, "packet")
+        e1 = rule12_error(G1, S1, spec.nvar)
+        outs = [gpu_one_step(spec, U0, dt, B.ORCHA_TASK_HYDRO_RK2, tile, p) for p in ("packet", "batch")]
+        e = max(rule12_error(G, O, spec.nvar) for G in outs)
+        print(f"  tile {tile}: stage 1 rule-12 error {e1:.3e}, Heun step {e:.3e}")
+        assert e1 <= TOL and e <= TOL
+        assert np.array_equal(outs[0], outs[1])

@@ -70,8 +70,9 @@ def test_sedov_128_packets_of_64_10_steps(oracle_mod):
 
 @pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 0, 1)])
 def test_random_jumps_every_tile_shape(oracle_mod, periodic):
-    """Random jumps (limiter, upwind and first-order fallback branches); every
-    tile variant gives the same bits."""
+    """Random jumps (limiter and upwind branches; the first-order fallback is
+    driven in tests/test_gpu_fallback.py); every tile variant gives the same
+    bits."""
     spec = wl.MeshSpec(ndim=3, nb=(2, 2, 2), bs=(16, 16, 16), periodic=periodic)
     U0 = wl.random_blocky_state(spec, 17)
     O, _ = oracle_steps(oracle_mod, spec, U0, 4)
