@@ -21,22 +21,32 @@ namespace orcha {
 // (512 KiB) until the process exits.
 static __device__ __align__(256) unsigned long long g_noalloc_smax[ORCHA_NOALLOC_MAX_BLOCKS];
 
-// Device address of g_noalloc_smax on each device, looked up once per device
-// with that device current (host code must never pass the symbol itself).
+// Device address of g_noalloc_smax in the current context. Host code must
+// never pass the symbol itself. Outside stream capture the address is looked
+// up on every call (cheap once the module is loaded), so a context the caller
+// reset or replaced since an earlier call never gets a stale pointer. Inside
+// a capture the lookup could load the module, which capture forbids, so the
+// address that the last uncaptured call on this device saw is used.
 static std::mutex g_addr_mu;
 static unsigned long long* g_addr[64] = {};
 
-static orcha_status scratch_address(unsigned long long** out) {
+static orcha_status scratch_address(cudaStream_t s, unsigned long long** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cfl_dt_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= 64) return set_error(ORCHA_ERR_UNSUPPORTED, "cfl_dt_noalloc: device index above 63");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_error(e, "cfl_dt_noalloc: cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lock(g_addr_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_smax);
         if (e != cudaSuccess) return cuda_error(e, "cfl_dt_noalloc: cudaGetSymbolAddress");
         g_addr[dev] = static_cast<unsigned long long*>(p);
+    } else if (!g_addr[dev]) {
+        return set_error(ORCHA_ERR_INVALID,
+                         "cfl_dt_noalloc: the first call on a device must come before any stream capture");
     }
     *out = g_addr[dev];
     return ORCHA_OK;
@@ -62,11 +72,11 @@ extern "C" orcha_status orcha_cfl_dt_noalloc(const orcha_mesh_desc* desc, int32_
                  nblk, ORCHA_NOALLOC_MAX_BLOCKS);
         return orcha::set_error(ORCHA_ERR_INVALID, msg);
     }
+    cudaStream_t s = (cudaStream_t)stream;
     unsigned long long* smax = nullptr;
-    if ((st = orcha::scratch_address(&smax))) return st;
+    if ((st = orcha::scratch_address(s, &smax))) return st;
     m.smax = smax;
     m.err = err_dev;
-    cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: clear the slots this call raises
     cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned long long) * (size_t)nblk, s);
     if (e != cudaSuccess) return orcha::cuda_error(e, "cfl_dt_noalloc: clear");
