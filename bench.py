@@ -1,16 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the block-hydro packet path; prints one JSON line.
 
-Default workload (one bench step): 3D Sedov blast on 128^3 cells as 512
-blocks of 16^3 interior cells (+2 guard layers), FP64, packets of 64 blocks,
-10 time steps: pack the initial state into the padded layout, form dt, then
-per time step guard fill + hydro task on every packet + dt reduction, and
-unpack the result. Metric: zone-updates/s (interior cells x time steps / s).
+Default workload (one bench step): 3D Sedov blast on 256^3 cells as 4096
+blocks of 16^3 interior cells (+2 guard layers), FP64, in packets of
+seed-uniform 1..256 blocks, 10 time steps: pack the initial state into the
+padded layout, form dt, then one persistent launch per time step over every
+packet (halo gather, hydro task, fused dt reduction), and unpack the result.
+Metric: zone-updates/s (interior cells x time steps / s). The line also
+carries the serving latency (p50/p99 per request) of a Poisson request
+stream through the continuous-batching server and through plain
+per-request launches.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov128|sedov256_uneven|sedov128_f32|sedov128_ff|sedov256_uneven_ff|sedov128_rk2|
-                     sedov128_rk2_f32|sedov128_rk2_ff]
-                    [--no-cpu-baseline]
+                    [--workload sedov256_uneven|sedov128|sedov128_f32|sedov128_f32x|sedov128_ff|sedov256_uneven_ff|
+                     sedov128_rk2|sedov128_rk2_f32|sedov128_rk2_ff]
+                    [--no-cpu-baseline] [--no-serving] [--serve-requests N]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
 of the workload (the path has no exchange step between replicas); `value` is
@@ -95,12 +99,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sedov128",
-                    choices=["sedov128", "sedov128_f32", "sedov256_uneven", "sedov128_ff", "sedov256_uneven_ff",
+    ap.add_argument("--workload", default="sedov256_uneven",
+                    choices=["sedov128", "sedov128_f32", "sedov128_f32x", "sedov256_uneven", "sedov128_ff",
+                             "sedov256_uneven_ff",
                              "sedov128_rk2", "sedov128_rk2_f32", "sedov128_rk2_ff"])
     ap.add_argument("--tile", default="", choices=["", "8x8", "16x8", "16x16"],
                     help="column tile of the hydro kernel (default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", default="1000,50000",
+                    help="arrival rates (requests/s) of the serving leg: one below and one above saturation")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-threads", type=int, default=0,
                     help="host threads of the oracle in the reference arm (0: all)")
@@ -117,7 +126,8 @@ def workload(name):
         spec, packets = wl.sedov256_uneven_packets(0)
         desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
         nt = 10
-    task = "f32flux" if name.endswith("_f32") else "ff" if name.endswith("_ff") else "fp64"
+    task = ("f32flux" if name.endswith("_f32") else "f32flux_ffsum" if name.endswith("_f32x")
+            else "ff" if name.endswith("_ff") else "fp64")
     if "_rk2" in name:
         import dataclasses
         task = {"fp64": "rk2", "f32flux": "rk2_f32", "ff": "rk2_ff"}[task]
@@ -126,11 +136,12 @@ def workload(name):
     return spec, packets, nt, task, desc
 
 
-DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 update",
+DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 flux differences, update and signal speed",
+          "f32flux_ffsum": "f32 reconstruction/flux + float-float flux sums + f64 update (f32 signal speed)",
           "ff": "double-word f32x2 reconstruction/flux + f64 update", "rk2": "f64",
-          "rk2_f32": "f32 reconstruction/flux + f64 update (Heun RK2)",
+          "rk2_f32": "f32 reconstruction/flux + f64 flux differences and update (Heun RK2)",
           "rk2_ff": "double-word f32x2 reconstruction/flux + f64 update (Heun RK2)"}
-KTYPES = {"fp64": "rd", "f32flux": "float", "ff": "dw", "rk2": "rd,true", "rk2_f32": "float,true",
+KTYPES = {"fp64": "rd", "f32flux": "float", "f32flux_ffsum": "float,false,true", "ff": "dw", "rk2": "rd,true", "rk2_f32": "float,true",
           "rk2_ff": "dw,true"}
 
 
@@ -264,6 +275,35 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving latency
+
+def serving_latency(args):
+    """p50/p99 request latency and zone-updates/s of a Poisson stream of
+    serving requests (K ~ U[1, 512] blocks of 8^3/16^3/32^3, one step each,
+    FP32 flux, 64 GB pool) at one rate the GPU keeps up with and one above
+    saturation, through the continuous-batching server and through plain
+    per-request launches (a mesh, a packet and per-step launches each)."""
+    from paper_2507_09337_b300 import binding as B
+    from paper_2507_09337_b300 import serve
+    from paper_2507_09337_b300 import workloads as wl
+    task = B.ORCHA_TASK_HYDRO_F32FLUX
+    base = wl.serving_stream(args.serve_requests, 1.0)
+    out = {"requests": args.serve_requests, "task": "f32flux", "budget_gb": 64,
+           "workload": "Poisson arrivals; K ~ U[1, 512] blocks of 8^3, 16^3 or 32^3; Sedov-like or Sod-like; "
+                       "1 step each; latency = completion - submission", "rates": []}
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        stream = [(t / rate, req) for t, req in base]
+        srv = serve.run_server(stream, task, 64 * 10 ** 9)
+        pln = serve.run_plain(stream, task)
+        out["rates"].append({
+            "rate_per_s": rate,
+            "server": {"p50_ms": srv["p50_ms"], "p99_ms": srv["p99_ms"], "zone_updates_per_s": srv["zone_updates_per_s"],
+                       "pool_peak_gb": srv["pool_peak_gb"]},
+            "plain": {"p50_ms": pln["p50_ms"], "p99_ms": pln["p99_ms"], "zone_updates_per_s": pln["zone_updates_per_s"]},
+        })
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
@@ -366,41 +406,44 @@ def main():
     zones_per_launch = tot_zones / len(durs)
     hydro_share = tot_s / (ms * 1e-3)
     fp64_bound = task_name in ("fp64", "rk2")
+    hbm_peak, hbm_src = 6400.0, "fallback 6.4 TB/s (MEASURED_PEAKS.json absent)"
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        hbm_src = "measured copy bandwidth (MEASURED_PEAKS.json)"
+    kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
+    prof = {"sedov128": "persistent_kernel_fp64_sedov128.md",
+            "sedov256_uneven": "persistent_kernel_fp64_sedov256.md",
+            "sedov128_rk2": "persistent_kernel_rk2_sedov128.md",
+            "sedov128_f32": "persistent_kernel_f32flux_sedov128.md",
+            "sedov128_ff": "persistent_kernel_ff_sedov128.md"}.get(args.workload)
+    traffic = profiled_traffic(prof, kname) if prof else None
     if fp64_bound:
+        # the FP64 pipe bounds this task: its peak is measured here, on this
+        # GPU, by the library's FMA throughput probe (lane operations/s)
+        fp64_peak = B.orcha_measure_fp64_rate(0) / 1e12
         flops = FLOPS_PER_ZONE_3D_RK2 if task_name == "rk2" else FLOPS_PER_ZONE_3D
         achieved = flops * zones_per_launch / avg_launch_s / 1e12
-        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
         # RK2: the recorded traffic is per time step (its two stage launches)
-        prof = {"sedov128": "persistent_kernel_fp64_sedov128.md",
-                "sedov128_rk2": "persistent_kernel_rk2_sedov128.md"}.get(args.workload)
-        traffic = profiled_traffic(prof, kname) if prof else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic,
                 "kernel": kname, "per_launch": "one time step of all packets" + (
                     " (two stage launches)" if task_name == "rk2" else ""),
-                "peak_source": "FP64 2 lanes/SM/clk x 148 SMs x 2032 MHz (non-FMA ops); FP64-ALU bound"}
+                "ops_per_zone": flops,
+                "peak_source": "measured: FP64 FMA throughput probe (orcha_measure_fp64_rate) on this GPU, "
+                               "lane operations/s; the task's operations are counted in the same unit "
+                               f"(nominal 2 lanes/SM/clk x 148 SMs x 2032 MHz = {FP64_PEAK_TFLOPS:.3f} T)"}
     else:
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
         # a Heun step is two launches: stage 1 reads and writes the state (80 B
         # per zone), stage 2 also reads the step's initial state (120 B)
         rk = task_name.startswith("rk2")
         bytes_per_zone = BYTES_PER_ZONE_3D_RK2_STEP if rk else BYTES_PER_ZONE_3D
         achieved = bytes_per_zone * zones_per_launch / avg_launch_s / 1e9
-        kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
-        prof = {"sedov128_f32": "persistent_kernel_f32flux_sedov128.md",
-                "sedov128_ff": "persistent_kernel_ff_sedov128.md"}.get(args.workload)
-        traffic = profiled_traffic(prof, kname) if prof else None
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": kname}
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic, "kernel": kname, "peak_source": hbm_src}
         if rk:
             roof["per_launch"] = "one time step of all packets (two stage launches)"
-    hbm_peak = 6489.3
-    try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except Exception:
-        pass
     hbm_eff = BYTES_PER_ZONE_3D * value / world / 1e9
+    spec_state_mb = mesh.state[0].numel() * 8 / 1e6
 
     # end to end through the public API with host buffers: every step copies its
     # input from pinned host memory and its result back. Three meshes on three
@@ -460,11 +503,15 @@ def main():
         "config": {"workload": desc, "task": task_name, "zones_per_step": spec.zones * nt,
                    "tile": (f"{tile[0]}x{tile[1]} (--tile)" if args.tile else
                             f"{tile[0]}x{tile[1]} (autotuned, {tile[2]:.3f} ms/step on the tuning mesh)"),
-                   "l2": "inputs larger than L2 (two 164 MB state buffers + 84 MB initial state)",
+                   "l2": (f"inputs larger than L2 (two {spec_state_mb:.0f} MB state buffers + "
+                          f"{U0_host.nbytes / 1e6:.0f} MB initial state)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "hydro_share_of_step": hydro_share,
-                   "hbm": {"algorithmic_gbs": hbm_eff, "peak_gbs": hbm_peak, "frac": hbm_eff / hbm_peak,
-                           "bytes_per_zone": BYTES_PER_ZONE_3D}},
+                   "hbm": {"algorithmic_gbs": hbm_eff, "bytes_per_zone": BYTES_PER_ZONE_3D,
+                           "frac_of_measured": hbm_eff / hbm_peak, "measured_gbs": hbm_peak,
+                           "frac_of_8tbs": hbm_eff / 8000.0,
+                           "target": ">= 0.60 of the 8 TB/s HBM roofline",
+                           "target_met": hbm_eff / 8000.0 >= 0.60}},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_io,
@@ -473,6 +520,8 @@ def main():
                                                          "take turns so copies overlap compute"},
         "gpu_launches": launches_per_step * args.steps,
     }
+    if not args.no_serving:
+        line["latency"] = serving_latency(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, n, el = oracle_rate(spec, U0_host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",

@@ -95,10 +95,12 @@ typedef enum {
      * library built with ORCHA_FP64_CONTRACT=0 (liborcha_exact.so) fuses
      * nothing and reproduces an unfused FP64 evaluation bit for bit. */
     ORCHA_TASK_HYDRO_FP64 = 1,
-    /* As HYDRO_FP64 with reconstruction, predictor and HLL fluxes in FP32
-     * (from the FP64 state rounded to nearest); each face flux is promoted to
-     * FP64 before the conservative update, which is FP64, as are the guard
-     * fill and the dt reduction. */
+    /* As HYDRO_FP64 with primitives, reconstruction, predictor and HLL fluxes
+     * in FP32 (from the FP64 state rounded to nearest). Each face flux is
+     * promoted to FP64 before the difference; the differences, their dt/dx_d
+     * scaling, the x+y+z sum and the conservative update are FP64, as are the
+     * guard fill, the new state's per-cell signal speed and the dt
+     * reduction. */
     ORCHA_TASK_HYDRO_F32FLUX = 2,
     /* Only the blocks' largest signal speed of the current buffer (to form
      * the first time step). */
@@ -127,8 +129,8 @@ typedef enum {
     ORCHA_TASK_HYDRO_RK2 = 7,
     /* The two Heun stages and the whole Heun step with the plain MUSCL
      * operator evaluated as in HYDRO_F32FLUX (FP32 primitives, slopes and HLL
-     * fluxes, float-float flux sums, FP64 update, stage-2 average and dt; the
-     * step's first dt by the FP32 signal-speed rule). */
+     * fluxes; FP64 flux differences, update, stage-2 average, signal speed
+     * and dt). */
     ORCHA_TASK_RK2_F32FLUX_STAGE1 = 8,
     ORCHA_TASK_RK2_F32FLUX_STAGE2 = 9,
     ORCHA_TASK_HYDRO_RK2_F32FLUX = 10,
@@ -136,7 +138,16 @@ typedef enum {
      * arithmetic on the FP32 pipe, FP64 update, stage-2 average and dt). */
     ORCHA_TASK_RK2_FF_STAGE1 = 11,
     ORCHA_TASK_RK2_FF_STAGE2 = 12,
-    ORCHA_TASK_HYDRO_RK2_FF = 13
+    ORCHA_TASK_HYDRO_RK2_FF = 13,
+    /* HYDRO_F32FLUX with a cheaper update: each difference dt/dx_d (F_hi -
+     * F_lo) of the FP32 face fluxes is formed exactly as a float pair and the
+     * x+y+z sum is float-float (about 46 bits, within ~1e-14 of the summed
+     * terms); only U+ = U - sum is FP64. The new state's signal speed is
+     * evaluated in FP32 and rounded up by 1 + 2^-18 (FP64 where the FP32
+     * pressure is not positive); the max-reduction and dt = cfl / max stay
+     * FP64, and the first dt uses the same rule. Not in the paper: it moves
+     * the per-cell FP64 work off this GPU's scarce FP64 pipe. */
+    ORCHA_TASK_HYDRO_F32FLUX_FFSUM = 14
 } orcha_task;
 
 /* Mesh geometry and the caller's device buffers. */
@@ -242,9 +253,10 @@ ORCHA_API orcha_status orcha_dt_reduce(orcha_mesh* mesh, void* stream);
  *   if (init_dt) SIGNAL_SPEED on every packet, dt_reduce;
  *   repeat nsteps: GUARD_FILL on every packet; hydro_task on every packet;
  *                  dt_reduce; swap.
- * For HYDRO_F32FLUX the first dt uses that task's FP32 signal-speed rule
- * (as every later step's dt does); otherwise the FP64 SIGNAL_SPEED task.
- * hydro_task: HYDRO_FP64, HYDRO_F32FLUX, HYDRO_FF, or HYDRO_RK2, whose step
+ * For HYDRO_F32FLUX_FFSUM the first dt uses that task's FP32 signal-speed
+ * rule (as every later step's dt does); otherwise the FP64 SIGNAL_SPEED task.
+ * hydro_task: HYDRO_FP64, HYDRO_F32FLUX, HYDRO_F32FLUX_FFSUM, HYDRO_FF, or
+ * HYDRO_RK2 (and its FP32-flux and double-word forms), whose step
  * is GUARD_FILL, RK2_STAGE1, swap, GUARD_FILL, RK2_STAGE2, dt_reduce, swap
  * (the current buffer is the same before and after a step).
  * use_graph != 0 captures the nsteps-step sequence in a CUDA graph the first
@@ -306,7 +318,7 @@ typedef struct orcha_request_desc {
     int32_t ndim, nb[3], bs[3], periodic[3]; /* as in orcha_mesh_desc */
     double gamma, cfl, lo[3], hi[3];
     int32_t nsteps;           /* time steps to advance (>= 1); the first dt comes from the initial state */
-    int32_t task;             /* ORCHA_TASK_HYDRO_FP64, _F32FLUX or _FF */
+    int32_t task;             /* ORCHA_TASK_HYDRO_FP64, _F32FLUX, _F32FLUX_FFSUM or _FF */
     int32_t init_kind;        /* ORCHA_INIT_* */
     int32_t region[4];
     double u_in[5], u_out[5]; /* conserved states (rho, m_x, m_y[, m_z], E) of the recipes */
@@ -332,7 +344,10 @@ typedef struct orcha_server_stats {
 
 /* Reserve a device pool of hbm_budget_bytes and start the worker on the
  * current device. max_active bounds the requests holding device memory at
- * once. Errors: INVALID, OOM, CUDA. */
+ * once. The pool also holds the step loop's work lists, sized here once
+ * (two in-flight steps x (max_active request slots + one 16-byte item per
+ * 4 KiB of pool), about 0.8 % of the budget), so the worker never allocates
+ * or frees device memory while serving. Errors: INVALID, OOM, CUDA. */
 ORCHA_API orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, orcha_server** out);
 /* Stop the worker, wait for the device, free everything. Requests not yet
  * waited for are dropped. */
@@ -378,9 +393,12 @@ ORCHA_API orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_t
  * The caller passes the inputs and outputs: desc (geometry, state buffers,
  * dt_dev) and err_dev, a device int32 into which ORCHA_DEVERR_* bits are
  * OR-ed (the caller clears it); guards need not be filled.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Every call shares the one array and clears the entries it uses
+ * Each call outside stream capture looks up the array's device address in
+ * the current context (so a context reset between calls is safe); a call
+ * made while `stream` is capturing reuses the address that the last
+ * uncaptured call on this device saw, so make a first call on each device
+ * before any stream capture (a capture after a context reset needs another
+ * uncaptured call first). Every call shares the one array and clears the entries it uses
  * at its start, so calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller. Asynchronous on
  * `stream`. Errors: INVALID (descriptor, buffers, size limit), UNSUPPORTED,
@@ -422,6 +440,16 @@ ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t se
  * [3] reciprocal, [4] reciprocal square root, [5] sound speed
  * sqrt(x / rho) (relative). Synchronous. Errors: INVALID, CUDA. */
 ORCHA_API orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, double max_err[6]);
+
+/* Diagnostics: the FP64 pipe's throughput on the current device, in lane
+ * operations per second (one FMA, add or multiply = one operation): op 0
+ * FMA, 1 add, 2 multiply. Every SM runs its maximum resident warps, each
+ * thread eight independent chains of the operation; best of five timed
+ * launches after one warm-up (about 0.1 s each). This is the ceiling of the
+ * FP64 hydro task, which the FP64 pipe bounds on this GPU (the task's
+ * operations per zone are counted in the same unit). Synchronous; allocates
+ * and frees 8 bytes and one stream. Errors: INVALID, CUDA. */
+ORCHA_API orcha_status orcha_measure_fp64_rate(int32_t op, double* lane_ops_per_s);
 
 /* Message of the last error returned on this thread ("" if none). */
 ORCHA_API const char* orcha_last_error(void);

@@ -46,12 +46,14 @@ ORCHA_TASK_HYDRO_RK2_F32FLUX = 10
 ORCHA_TASK_RK2_FF_STAGE1 = 11
 ORCHA_TASK_RK2_FF_STAGE2 = 12
 ORCHA_TASK_HYDRO_RK2_FF = 13
+ORCHA_TASK_HYDRO_F32FLUX_FFSUM = 14
 
 ORCHA_INIT_FROM_HOST = 0
 ORCHA_INIT_SPHERE = 1
 ORCHA_INIT_HALF_SPACE = 2
 
 TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF,
+         "f32flux_ffsum": ORCHA_TASK_HYDRO_F32FLUX_FFSUM,
          "rk2": ORCHA_TASK_HYDRO_RK2, "rk2_f32": ORCHA_TASK_HYDRO_RK2_F32FLUX, "rk2_ff": ORCHA_TASK_HYDRO_RK2_FF}
 
 
@@ -144,6 +146,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_fp64_emulation": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_dword": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "orcha_measure_fp64_rate": (_st, [_i32, ctypes.POINTER(ctypes.c_double)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
 
@@ -348,6 +351,14 @@ def orcha_selftest_dword(count: int, seed: int = 1) -> list:
     err = (ctypes.c_double * 6)()
     _check(lib().orcha_selftest_dword(int(count), int(seed), err))
     return list(err)
+
+
+def orcha_measure_fp64_rate(op: int = 0) -> float:
+    """FP64 pipe throughput of the current device in lane operations/s
+    (op 0 FMA, 1 add, 2 multiply)."""
+    r = ctypes.c_double()
+    _check(lib().orcha_measure_fp64_rate(int(op), ctypes.byref(r)))
+    return r.value
 
 
 def orcha_last_error() -> str:

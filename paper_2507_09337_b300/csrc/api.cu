@@ -336,6 +336,7 @@ orcha_status orcha_packet_run(orcha_packet* p, orcha_task task, void* stream) {
         case ORCHA_TASK_GUARD_FILL: e = orcha::launch_guard_fill(m->dev, p->ids_dev, p->n, cur, st); break;
         case ORCHA_TASK_HYDRO_FP64:
         case ORCHA_TASK_HYDRO_F32FLUX:
+        case ORCHA_TASK_HYDRO_F32FLUX_FFSUM:
         case ORCHA_TASK_HYDRO_FF:
         case ORCHA_TASK_RK2_STAGE1:
         case ORCHA_TASK_RK2_STAGE2:

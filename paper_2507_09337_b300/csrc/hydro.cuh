@@ -202,8 +202,9 @@ __device__ __forceinline__ unsigned long long block_signal_speed(const MeshDev& 
 }
 
 // Signal speed sum_d (|u_d| + c) / dx_d of one new FP64 state, as the bits of
-// a non-negative double; raises the non-physical flag. FP64 path: the
-// definition's expression tree. FP32-flux path: evaluated in FP32 from the
+// a non-negative double; raises the non-physical flag. T = rd: the
+// definition's expression tree (FP64 and FP32-flux tasks). T = float (the
+// FP32-flux shortcut): evaluated in FP32 from the
 // state rounded to nearest and rounded up by a factor 1 + 2^-18 (above the
 // few-ulp error of that evaluation), so dt = cfl / max never exceeds the FP64
 // value by more than rounding; a cell whose FP32 pressure is not positive is
@@ -235,10 +236,10 @@ __device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, 
     return (unsigned long long)bits(s);   // s >= 0 or NaN
 }
 
-// The FP32-flux variant's signal speed (new_state_speed<float>: FP32, rounded
+// The FP32-flux shortcut's signal speed (new_state_speed<float>: FP32, rounded
 // up by 1 + 2^-18, FP64 where the FP32 pressure is not positive) over the
 // interior cells of block `blk` handled by this thread; the first time step
-// of an FP32-flux run comes from the same rule as every later one.
+// of a shortcut run comes from the same rule as every later one.
 __device__ __forceinline__ unsigned long long block_signal_speed_f32(const MeshDev& m, int blk,
                                                                      const double* __restrict__ U, int chunk = 0,
                                                                      int nchunks = 1) {
@@ -305,7 +306,14 @@ struct Tile {
 // step). stage 1: Uout = Uin + dt L(Uin); stage 2: Uout = 0.5 * (Uout +
 // (Uin + dt L(Uin))), the old Uout (the step's initial state) read at the
 // cell just before it is overwritten. Stage 1 raises no signal speed.
-template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false>
+//
+// FX (T = float only): the FP32-flux variant's shortcut update. By default
+// (FX = false) the FP32 face fluxes are promoted to FP64 before the
+// difference and the difference, its dt/dx scaling, the x+y+z sum, the
+// update and the new state's signal speed are FP64, as for T = rd. With FX
+// the differences are formed exactly in float-float, summed to ~46 bits, and
+// the signal speed is evaluated in FP32 (rounded up by 1 + 2^-18).
+template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false, bool FX = false>
 __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
                                            const double* __restrict__ Uin, double* __restrict__ Uout,
                                            unsigned char* smem_raw, unsigned long long* red, int z0 = 0,
@@ -651,16 +659,19 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     };
 
     // z state carried by the owner: high-z face state of the previous plane,
-    // its low-z face flux, and its x+y flux-difference sum. FP64 path: the sum
-    // in FP64 from the promoted face fluxes, as the definition writes it.
-    // FP32-flux path: each difference c_d (F_hi - F_lo) of FP32 face fluxes is
+    // its low-z face flux, and its x+y flux-difference sum. FP64 and FP32-flux
+    // paths: the sum in FP64 from the face fluxes promoted to FP64, as the
+    // definition writes it. FP32-flux shortcut (FX): each difference
+    // c_d (F_hi - F_lo) of FP32 face fluxes is
     // formed exactly (two_sum) and scaled by c_d held as a float pair, and the
     // x, y, z terms are summed as float-float (about 46 bits); only the final
     // U+ = U - (sum) is FP64 arithmetic. The same face value enters both cells,
     // so the sum still telescopes to ~1e-14 of each term.
     // FF path: the differences and their c_d scaling and sum are double-word,
     // the final U+ = U - (sum) FP64.
-    constexpr bool F32 = std::is_same<T, float>::value;
+    static_assert(!FX || std::is_same<T, float>::value, "the shortcut update exists for FP32 fluxes only");
+    constexpr bool F32 = std::is_same<T, float>::value && FX;     // float-float flux sums
+    using SpeedT = typename std::conditional<F32, float, rd>::type;   // signal-speed rule of the new state
     constexpr bool DW = std::is_same<T, dw>::value;
     T zp_prev[NV], Fz_prev[NV];
     double acc_prev[NV];
@@ -678,7 +689,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     dw cdw[3];                           // c_d as double-words (FF path)
 #pragma unroll
     for (int d = 0; d < 3; ++d) cdw[d] = DW ? P<dw>::in(cd[d]) : dw{0.0f, 0.0f};
-    float ch[3], cl[3];                  // c_d = dt/dx_d as float pairs (FP32-flux path)
+    float ch[3], cl[3];                  // c_d = dt/dx_d as float pairs (FP32-flux shortcut)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         ch[d] = d2f_rn(cd[d]);
@@ -804,7 +815,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                         if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                         Ob[gi + v * vs] = Un[v].v;
                     }
-                    if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                    if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
                 }
                 // leaving a block (or the item's range): raise its signal speed
                 // (CTA-uniform: every thread takes part, non-owners with 0)
@@ -850,7 +861,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                     if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
                     Ob[gi + v * vs] = Un[v].v;
                 }
-                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<T, NDIM>(m, Un));
+                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
             }
         }
     }
@@ -861,7 +872,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
 // Packet path: one CTA per (packet block, column tile); guards come from the
 // padded block.
-template <int NDIM, int TX, int TY, class T, bool RK = false>
+template <int NDIM, int TX, int TY, class T, bool RK = false, bool FX = false>
 __global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<T, RK>())
 hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
              const double* __restrict__ Uin, double* __restrict__ Uout, int stage) {
@@ -870,7 +881,7 @@ hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int 
     const int ntile = tiles_x * tiles_y;
     const int blk = blk_ids[blockIdx.x / ntile];
     const int tile = blockIdx.x % ntile;
-    hydro_tile<NDIM, TX, TY, T, false, RK>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY, Uin, Uout,
+    hydro_tile<NDIM, TX, TY, T, false, RK, FX>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY, Uin, Uout,
                                            smem_raw, red, 0, -1, stage);
 }
 

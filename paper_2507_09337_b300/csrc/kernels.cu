@@ -258,6 +258,21 @@ cudaError_t launch_region_init(const MeshDev& m, double* U, int kind, int4 reg, 
     return cudaGetLastError();
 }
 
+// Full-block work items of the meshes slots[0..nslots): slot s owns items
+// item0 .. item0 + nitems - 1 in block-major, tile-minor order (one CTA per
+// slot), the order a host-built list of the same meshes has.
+__global__ void expand_items_kernel(const SlotDev* __restrict__ slots, Item* __restrict__ items) {
+    const SlotDev& sd = slots[blockIdx.x];
+    const int nt = sd.tiles_x * sd.tiles_y, n = sd.nitems, base = sd.item0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) items[base + i] = Item{(int)blockIdx.x, i / nt, i % nt, 0};
+}
+
+cudaError_t launch_expand_items(const SlotDev* slots, int nslots, Item* items, cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    expand_items_kernel<<<nslots, 256, 0, st>>>(slots, items);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_totals(const MeshDev& m, int nblk, const double* U, double* partial, double* out, cudaStream_t st) {
     block_totals_kernel<<<dim3((unsigned)nblk, (unsigned)m.nvar), 256, 0, st>>>(m, U, partial);
     cudaError_t e = cudaGetLastError();
@@ -406,49 +421,51 @@ cudaError_t launch_selftest(unsigned long long lo, unsigned long long n, unsigne
 
 // ---------------------------------------------------------------- hydro launch table
 // Variant of a precision code: arithmetic type and whether the kernel runs
-// Runge-Kutta stages (plain MUSCL; kRK2 FP64, kRK2F32 FP32 flux, kRK2FF double-word).
-template <int NDIM, int TX, int TY, class T, bool RK>
+// Runge-Kutta stages (plain MUSCL; kRK2 FP64, kRK2F32 FP32 flux, kRK2FF
+// double-word); kF32X is the FP32-flux shortcut update (FX).
+template <int NDIM, int TX, int TY, class T, bool RK, bool FX = false>
 static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout,
                                   int stage, cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    auto kern = hydro_kernel<NDIM, TX, TY, T, RK>;
+    auto kern = hydro_kernel<NDIM, TX, TY, T, RK, FX>;
     const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
     kern<<<dim3((unsigned)(n * tx * ty)), dim3(Tl::template nb<T, RK>()), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage);
     return cudaGetLastError();
 }
 
-template <int NDIM, int TX, int TY, class T, bool RK>
+template <int NDIM, int TX, int TY, class T, bool RK, bool FX = false>
 static cudaError_t configure_t() {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    cudaError_t e = cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T, RK>,
+    cudaError_t e = cudaFuncSetAttribute(hydro_kernel<NDIM, TX, TY, T, RK, FX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(persistent_kernel<NDIM, TX, TY, T, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(persistent_kernel<NDIM, TX, TY, T, RK, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
 }
 
-template <int NDIM, int TX, int TY, class T, bool RK>
+template <int NDIM, int TX, int TY, class T, bool RK, bool FX = false>
 static cudaError_t launch_persistent_t(const SlotDev* slots, const Item* items, int nitems, unsigned* queue, int grid,
                                        int stage, cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    persistent_kernel<NDIM, TX, TY, T, RK><<<grid, Tl::template nb<T, RK>(), smem, st>>>(slots, items, nitems, queue, stage);
+    persistent_kernel<NDIM, TX, TY, T, RK, FX><<<grid, Tl::template nb<T, RK>(), smem, st>>>(slots, items, nitems, queue, stage);
     return cudaGetLastError();
 }
 
-template <int NDIM, int TX, int TY, class T, bool RK>
+template <int NDIM, int TX, int TY, class T, bool RK, bool FX = false>
 static cudaError_t occupancy_t(int* per_sm) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T, RK>, Tl::template nb<T, RK>(),
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persistent_kernel<NDIM, TX, TY, T, RK, FX>, Tl::template nb<T, RK>(),
                                                          smem);
 }
 
 #define ORCHA_PERS_CASE(ND, X, Y)                                                                         \
     if (ndim == ND && tx == X && ty == Y)                                                                 \
         return prec == kF32   ? launch_persistent_t<ND, X, Y, float, false>(slots, items, nitems, queue, grid, 0, st) \
+               : prec == kF32X ? launch_persistent_t<ND, X, Y, float, false, true>(slots, items, nitems, queue, grid, 0, st) \
                : prec == kFF  ? launch_persistent_t<ND, X, Y, dw, false>(slots, items, nitems, queue, grid, 0, st)    \
                : prec == kRK2 ? launch_persistent_t<ND, X, Y, rd, true>(slots, items, nitems, queue, grid, stage, st) \
                : prec == kRK2F32 ? launch_persistent_t<ND, X, Y, float, true>(slots, items, nitems, queue, grid, stage, st) \
@@ -469,6 +486,7 @@ cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev*
 #define ORCHA_OCC_CASE(ND, X, Y)                                                                       \
     if (ndim == ND && tx == X && ty == Y)                                                              \
         return prec == kF32   ? occupancy_t<ND, X, Y, float, false>(per_sm)                            \
+               : prec == kF32X ? occupancy_t<ND, X, Y, float, false, true>(per_sm)                     \
                : prec == kFF  ? occupancy_t<ND, X, Y, dw, false>(per_sm)                               \
                : prec == kRK2 ? occupancy_t<ND, X, Y, rd, true>(per_sm)                                \
                : prec == kRK2F32 ? occupancy_t<ND, X, Y, float, true>(per_sm)                          \
@@ -488,6 +506,7 @@ cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm
 #define ORCHA_TILE_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y)                                                              \
         return prec == kF32   ? launch_hydro_t<ND, X, Y, float, false>(m, ids, n, Uin, Uout, 0, st)    \
+               : prec == kF32X ? launch_hydro_t<ND, X, Y, float, false, true>(m, ids, n, Uin, Uout, 0, st) \
                : prec == kFF  ? launch_hydro_t<ND, X, Y, dw, false>(m, ids, n, Uin, Uout, 0, st)       \
                : prec == kRK2 ? launch_hydro_t<ND, X, Y, rd, true>(m, ids, n, Uin, Uout, stage, st)    \
                : prec == kRK2F32 ? launch_hydro_t<ND, X, Y, float, true>(m, ids, n, Uin, Uout, stage, st) \
@@ -509,6 +528,7 @@ cudaError_t launch_hydro(const MeshDev& m, int tx, int ty, int prec, const int* 
 #define ORCHA_CONF_CASE(ND, X, Y)                                                                      \
     if (ndim == ND && tx == X && ty == Y) {                                                            \
         cudaError_t e = configure_t<ND, X, Y, float, false>();                                         \
+        if (e == cudaSuccess) e = configure_t<ND, X, Y, float, false, true>();                         \
         if (e == cudaSuccess) e = configure_t<ND, X, Y, dw, false>();                                  \
         if (e == cudaSuccess) e = configure_t<ND, X, Y, rd, true>();                                   \
         if (e == cudaSuccess) e = configure_t<ND, X, Y, float, true>();                                \

@@ -13,17 +13,21 @@ namespace orcha {
 // reconstruction/flux or with double-word reconstruction/flux (all with the
 // FP64 update), and Heun Runge-Kutta stages (plain MUSCL) in the same three
 // arithmetics.
-enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3, kRK2F32 = 4, kRK2FF = 5 };
-constexpr int kNumPrec = 6;
+// kF32X: the FP32-flux shortcut (float-float flux sums, FP32 signal speed).
+enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3, kRK2F32 = 4, kRK2FF = 5, kF32X = 6 };
+constexpr int kNumPrec = 7;
 inline bool prec_is_rk(int p) { return p == kRK2 || p == kRK2F32 || p == kRK2FF; }
-// variants whose first dt uses the FP32 signal-speed rule
-inline bool prec_f32_dt(int p) { return p == kF32 || p == kRK2F32; }
+// variants whose first dt uses the FP32 signal-speed rule (the shortcut's)
+inline bool prec_f32_dt(int p) { return p == kF32X; }
+// variants with FP32 reconstruction and fluxes
+inline bool prec_is_f32(int p) { return p == kF32 || p == kF32X || p == kRK2F32; }
 inline bool prec_is_dw(int p) { return p == kFF || p == kRK2FF; }
 // Variant of a hydro task, or -1 for any other task.
 inline int prec_of(orcha_task t) {
     switch (t) {
         case ORCHA_TASK_HYDRO_FP64: return kF64;
         case ORCHA_TASK_HYDRO_F32FLUX: return kF32;
+        case ORCHA_TASK_HYDRO_F32FLUX_FFSUM: return kF32X;
         case ORCHA_TASK_HYDRO_FF: return kFF;
         case ORCHA_TASK_HYDRO_RK2:
         case ORCHA_TASK_RK2_STAGE1:
@@ -62,6 +66,7 @@ inline orcha_task rk_stage_task(orcha_task step, int k) {
 // Tasks that advance whole steps (mesh_advance, batch_advance, autotune).
 inline bool is_step_task(orcha_task t) {
     return t == ORCHA_TASK_HYDRO_FP64 || t == ORCHA_TASK_HYDRO_F32FLUX || t == ORCHA_TASK_HYDRO_FF ||
+           t == ORCHA_TASK_HYDRO_F32FLUX_FFSUM ||
            is_rk_step_task(t);
 }
 
@@ -119,6 +124,9 @@ constexpr int kTiles[3][2] = {{16, 16}, {16, 8}, {8, 8}};
 // One persistent launch (one time step of every mesh in `slots`).
 cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items,
                               int nitems, unsigned* queue, int grid, int stage, cudaStream_t st);
+// Full-block items of slots[0..nslots) written at items[slot.item0 ...]
+// (block-major, tile-minor), so a caller uploads only the slots.
+cudaError_t launch_expand_items(const SlotDev* slots, int nslots, Item* items, cudaStream_t st);
 // Resident CTAs per SM of a persistent variant.
 cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm);
 

@@ -32,6 +32,7 @@ struct SlotDev {
     int nitems;             // items of this mesh per launch
     int nblk;
     int tiles_x, tiles_y;
+    int item0;              // position of this mesh's first item (full-block items built on the device)
 };
 
 // One unit of work: a column tile of block blk over its interior planes, or,
@@ -92,8 +93,9 @@ template <int NB> struct MinBlocks<dw, NB> {
 };
 
 // RK = true: the launch is Runge-Kutta stage `stage` (1 or 2) of every mesh
-// (hydro_tile); the first stage leaves dt as it is.
-template <int NDIM, int TX, int TY, class T, bool RK = false>
+// (hydro_tile); the first stage leaves dt as it is. FX: the FP32-flux
+// variant's shortcut update (hydro_tile).
+template <int NDIM, int TX, int TY, class T, bool RK = false, bool FX = false>
 __global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<T, RK>(),
                                   (MinBlocks<T, Tile<NDIM, TX, TY>::template nb<T, RK>()>::value))
 persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ items, int nitems,
@@ -110,7 +112,7 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         const SlotDev& sd = slots[w.slot];
         const int cur = __ldcg(sd.cur);
         const int z0 = w.zr ? (w.zr & 0xFFFF) : 0, z1 = w.zr ? (w.zr >> 16) : -1;
-        hydro_tile<NDIM, TX, TY, T, true, RK>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX, (w.tile / sd.tiles_x) * TY,
+        hydro_tile<NDIM, TX, TY, T, true, RK, FX>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX, (w.tile / sd.tiles_x) * TY,
                                               sd.state[cur], sd.state[cur ^ 1], smem_raw, red, z0, z1, stage);
         if (threadIdx.x == 0) {
             __threadfence();

@@ -13,7 +13,8 @@
 //   step     ONE persistent launch that advances every active request by
 //            one time step (each with its own dt, formed on the device);
 //            requests join as soon as their admission completes and leave
-//            after their last step;
+//            after their last step; the work list's buffers are sized at
+//            creation (the loop allocates no device memory);
 //   complete finished requests on the copy stream: unpack, D2H, error word;
 //            their pool memory is released when the copy has landed.
 // At most two steps are in flight, so new requests join within two steps.
@@ -113,37 +114,40 @@ struct Req {
     orcha_request_stats stats{};
 };
 
-// One launch per (ndim 2 or 3) x (FP64, FP32 flux or FF) x tile kind (0: 8x8,
+// One launch per (ndim 2 or 3) x (FP64, FP32 flux, FF or FP32-flux shortcut) x tile kind (0: 8x8,
 // 1: 16x8, 2: 16x16): blocks 8 cells across x use the 8x8 tile; wider ones
 // the autotuner's choice for 16^3 blocks on a B300, 16x16 for FP64 and FF in
 // 3D when the blocks are 16 or more cells across y too, else 16x8.
-constexpr int kServePrec = 3;        // kF64, kF32, kFF (Runge-Kutta steps are not served)
+constexpr int kServePrec = 4;        // kF64, kF32, kFF, kF32X (Runge-Kutta steps are not served)
 constexpr int kTileKinds = 3;
 constexpr int kGroups = 2 * kServePrec * kTileKinds;
-__host__ __device__ constexpr int group_ndim(int g) { return 2 + (g & 1); }
-__host__ __device__ constexpr int group_prec(int g) { return (g >> 1) % kServePrec; }
-__host__ __device__ constexpr int group_kind(int g) { return (g >> 1) / kServePrec; }
-__host__ __device__ constexpr int group_tx(int g) { return group_kind(g) >= 1 ? 16 : 8; }
-__host__ __device__ constexpr int group_ty(int g) { return group_kind(g) == 2 ? 16 : 8; }
-constexpr int group_of(int ndim, int prec, int kind) { return (ndim - 2) | ((prec + kind * kServePrec) << 1); }
+constexpr int serve_index(int prec) { return prec == orcha::kF32X ? 3 : prec; }
+constexpr int served_prec(int i) { return i == 3 ? (int)orcha::kF32X : i; }
+constexpr int group_ndim(int g) { return 2 + (g & 1); }
+constexpr int group_prec(int g) { return served_prec((g >> 1) % kServePrec); }
+constexpr int group_kind(int g) { return (g >> 1) / kServePrec; }
+constexpr int group_tx(int g) { return group_kind(g) >= 1 ? 16 : 8; }
+constexpr int group_ty(int g) { return group_kind(g) == 2 ? 16 : 8; }
+constexpr int group_of(int ndim, int prec, int kind) { return (ndim - 2) | ((serve_index(prec) + kind * kServePrec) << 1); }
+constexpr bool serve_f32(int prec) { return prec == orcha::kF32 || prec == orcha::kF32X; }
 constexpr int tile_kind(int ndim, int prec, const int* bs) {
-    return bs[0] < 16 ? 0 : (ndim == 3 && prec != orcha::kF32 && bs[1] >= 16 ? 2 : 1);
+    return bs[0] < 16 ? 0 : (ndim == 3 && !serve_f32(prec) && bs[1] >= 16 ? 2 : 1);
 }
 static_assert(group_of(group_ndim(17), group_prec(17), group_kind(17)) == 17, "group index round trip");
+static_assert(group_of(group_ndim(23), group_prec(23), group_kind(23)) == 23, "group index round trip");
 
-struct GroupBuf {                    // host/device work list of one launch
-    std::vector<orcha::SlotDev> slots_h;
-    std::vector<orcha::Item> items_h;
-    orcha::SlotDev* slots_pin = nullptr;
-    orcha::Item* items_pin = nullptr;
-    orcha::SlotDev* slots_d = nullptr;
-    orcha::Item* items_d = nullptr;
-    unsigned* queue_d = nullptr;
-    size_t cap_slots = 0, cap_items = 0;
-};
-
-struct StepSlot {                    // one in-flight step: its launches and their buffers
-    GroupBuf g[kGroups];
+// Work-list buffers of one in-flight step, sized once at server creation so
+// the step loop never allocates: slots for at most max_active requests and
+// items for at most cap_items (an item needs at least 4 KiB of its request's
+// pool memory -- two state buffers over a tile of >= 64 cells x >= 4
+// variables x 8 bytes -- so pool bytes / 4096 items always suffice). The
+// device arrays are carved from the budgeted pool; each launch group takes
+// the next sub-range. Items are written on the device from the slots.
+struct StepSlot {
+    orcha::SlotDev* slots_pin = nullptr;     // host staging of the slots (pinned)
+    orcha::SlotDev* slots_d = nullptr;       // in the pool
+    orcha::Item* items_d = nullptr;          // in the pool
+    unsigned* queue_d = nullptr;             // in the pool: one work counter per group
     cudaEvent_t ev = nullptr;
     bool busy = false;
 };
@@ -168,6 +172,8 @@ struct orcha_server {
     std::vector<Req*> pending, admitting, active, finishing;
     StepSlot ring[kInflight];
     int ring_i = 0;
+    size_t cap_items = 0;                        // items one step can hold (see StepSlot)
+    long long items_held = 0;                    // items of the requests holding pool memory
     struct Result { double totals[5]; double dt; int err; int pad; };
     Result* res_pin = nullptr;                   // pinned results, one slot per live request
     std::vector<int> err_free;
@@ -201,8 +207,10 @@ bool orcha_server::fail(orcha_status s, const std::string& msg) {
 
 // Reserve pool memory for a request and enqueue its admission on the copy stream.
 bool orcha_server::admit(Req* r) {
+    if ((size_t)(items_held + r->nitems) > cap_items) return false;   // bounded by construction; kept as a guard
     const long long off = pool.alloc(r->bytes);
     if (off < 0) return false;   // does not fit now; retried when memory frees up
+    items_held += r->nitems;
     r->off = (size_t)off;
     char* p = pool.base + r->off;
     const size_t sb = round_up(r->state_elems * sizeof(double));
@@ -238,7 +246,7 @@ bool orcha_server::admit(Req* r) {
         SRV_CUDA(orcha::launch_region_init(r->m, r->state[0], r->d.init_kind, reg, rs, copy), "admit recipe");
     }
     SRV_CUDA(cudaMemsetAsync(tail, 0, tail_bytes, copy), "admit clear");
-    SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy, r->prec == orcha::kF32),
+    SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy, orcha::prec_f32_dt(r->prec)),
              "admit signal speed");
     SRV_CUDA(orcha::launch_dt_reduce(r->m, (int)r->nblk, r->dt, copy), "admit dt");
     SRV_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "admit event");
@@ -258,18 +266,16 @@ bool orcha_server::launch_step(bool* launched) {
         SRV_CUDA(q, "step slot");
         s.busy = false;
     }
+    // the slots of every group, group after group, into this step's staging
+    struct Span { int gi, slot0, nslots, item0, nitems; };
+    std::vector<Span> spans;
     std::vector<Req*> finished;
+    int nslot = 0, nitem = 0;
     for (int gi = 0; gi < kGroups; ++gi) {
-        const int ndim = group_ndim(gi), prec = group_prec(gi), gtx = group_tx(gi), gty = group_ty(gi);
-        GroupBuf& g = s.g[gi];
-        g.slots_h.clear();
-        g.items_h.clear();
-        std::vector<Req*> grp;
-        for (Req* r : active)
-            if (group_of(r->m.ndim, r->prec, r->kind) == gi) grp.push_back(r);
-        if (grp.empty()) continue;
-        for (size_t i = 0; i < grp.size(); ++i) {
-            Req* r = grp[i];
+        const int gtx = group_tx(gi), gty = group_ty(gi);
+        Span sp{gi, nslot, 0, nitem, 0};
+        for (Req* r : active) {
+            if (group_of(r->m.ndim, r->prec, r->kind) != gi) continue;
             orcha::SlotDev sd{};
             sd.m = r->m;
             sd.state[0] = r->state[0];
@@ -281,39 +287,30 @@ bool orcha_server::launch_step(bool* launched) {
             sd.nblk = (int)r->nblk;
             sd.tiles_x = r->m.bs[0] / gtx;
             sd.tiles_y = r->m.bs[1] / gty;
-            g.slots_h.push_back(sd);
-            const int nt = sd.tiles_x * sd.tiles_y;
-            for (int b = 0; b < (int)r->nblk; ++b)
-                for (int t = 0; t < nt; ++t) g.items_h.push_back({(int)i, b, t, 0});
-        }
-        if (g.slots_h.size() > g.cap_slots || g.items_h.size() > g.cap_items) {
-            // grow this launch's buffers (the slot is idle: its event has completed)
-            cudaFreeHost(g.slots_pin);
-            cudaFreeHost(g.items_pin);
-            cudaFree(g.slots_d);
-            cudaFree(g.items_d);
-            g.cap_slots = std::max(g.slots_h.size(), 2 * g.cap_slots);
-            g.cap_items = std::max(g.items_h.size(), 2 * g.cap_items);
-            SRV_CUDA(cudaMallocHost(&g.slots_pin, g.cap_slots * sizeof(orcha::SlotDev)), "grow");
-            SRV_CUDA(cudaMallocHost(&g.items_pin, g.cap_items * sizeof(orcha::Item)), "grow");
-            SRV_CUDA(cudaMalloc(&g.slots_d, g.cap_slots * sizeof(orcha::SlotDev)), "grow");
-            SRV_CUDA(cudaMalloc(&g.items_d, g.cap_items * sizeof(orcha::Item)), "grow");
-        }
-        if (!g.queue_d) SRV_CUDA(cudaMalloc(&g.queue_d, sizeof(unsigned)), "queue");
-        std::memcpy(g.slots_pin, g.slots_h.data(), g.slots_h.size() * sizeof(orcha::SlotDev));
-        std::memcpy(g.items_pin, g.items_h.data(), g.items_h.size() * sizeof(orcha::Item));
-        SRV_CUDA(cudaMemcpyAsync(g.slots_d, g.slots_pin, g.slots_h.size() * sizeof(orcha::SlotDev),
-                                 cudaMemcpyHostToDevice, compute), "step upload");
-        SRV_CUDA(cudaMemcpyAsync(g.items_d, g.items_pin, g.items_h.size() * sizeof(orcha::Item),
-                                 cudaMemcpyHostToDevice, compute), "step upload");
-        SRV_CUDA(cudaMemsetAsync(g.queue_d, 0, sizeof(unsigned), compute), "step queue");
-        const int grid = std::max(1, std::min((int)g.items_h.size(), occ[gi] * num_sms));
-        SRV_CUDA(orcha::launch_persistent(ndim, gtx, gty, prec, g.slots_d, g.items_d, (int)g.items_h.size(),
-                                          g.queue_d, grid, 0, compute), "step launch");
-        for (Req* r : grp) {
+            sd.item0 = sp.nitems;                      // relative to the group's first item
+            s.slots_pin[nslot++] = sd;
+            sp.nslots += 1;
+            sp.nitems += r->nitems;
             r->cur_host ^= 1;
             if (--r->steps_left == 0) finished.push_back(r);
         }
+        if (sp.nslots == 0) continue;
+        nitem += sp.nitems;
+        spans.push_back(sp);
+    }
+    if ((size_t)nitem > cap_items || nslot > max_active)
+        return fail(ORCHA_ERR_CUDA, "step: work list above its preallocated capacity");
+    SRV_CUDA(cudaMemcpyAsync(s.slots_d, s.slots_pin, (size_t)nslot * sizeof(orcha::SlotDev), cudaMemcpyHostToDevice,
+                             compute), "step upload");
+    SRV_CUDA(cudaMemsetAsync(s.queue_d, 0, sizeof(unsigned) * kGroups, compute), "step queues");
+    for (const Span& sp : spans) {
+        const int gi = sp.gi;
+        SRV_CUDA(orcha::launch_expand_items(s.slots_d + sp.slot0, sp.nslots, s.items_d + sp.item0, compute),
+                 "step items");
+        const int grid = std::max(1, std::min(sp.nitems, occ[gi] * num_sms));
+        SRV_CUDA(orcha::launch_persistent(group_ndim(gi), group_tx(gi), group_ty(gi), group_prec(gi),
+                                          s.slots_d + sp.slot0, s.items_d + sp.item0, sp.nitems, s.queue_d + gi,
+                                          grid, 0, compute), "step launch");
         std::lock_guard<std::mutex> lock(mu);
         totals.steps_launched += 1;
     }
@@ -399,6 +396,7 @@ void orcha_server::run() {
             cudaEventDestroy(r->ev);
             r->ev = nullptr;
             pool.release(r->off, r->bytes);
+            items_held -= r->nitems;
             const Result& res = res_pin[r->err_slot];
             r->stats.device_error = res.err;
             for (int v = 0; v < 5; ++v) r->stats.totals[v] = v < r->m.nvar ? res.totals[v] : 0.0;
@@ -437,8 +435,22 @@ orcha_status orcha_server_create(size_t hbm_budget_bytes, int32_t max_active, or
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(&s->res_pin, sizeof(orcha_server::Result) * (size_t)max_active);
-    for (int i = 0; e == cudaSuccess && i < kInflight; ++i)
-        e = cudaEventCreateWithFlags(&s->ring[i].ev, cudaEventDisableTiming);
+    // the step loop's work-list buffers, once: slots and items carved from the pool
+    s->cap_items = s->pool.size / 4096;
+    for (int i = 0; e == cudaSuccess && i < kInflight; ++i) {
+        StepSlot& r = s->ring[i];
+        e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(&r.slots_pin, sizeof(orcha::SlotDev) * (size_t)max_active);
+        const long long a = s->pool.alloc(sizeof(orcha::SlotDev) * (size_t)max_active);
+        const long long b = s->pool.alloc(sizeof(orcha::Item) * s->cap_items);
+        const long long c = s->pool.alloc(sizeof(unsigned) * kGroups);
+        if (e == cudaSuccess && (a < 0 || b < 0 || c < 0)) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) {
+            r.slots_d = (orcha::SlotDev*)(s->pool.base + a);
+            r.items_d = (orcha::Item*)(s->pool.base + b);
+            r.queue_d = (unsigned*)(s->pool.base + c);
+        }
+    }
     for (int nd = 2; e == cudaSuccess && nd <= 3; ++nd) {
         e = orcha::configure_hydro(nd, 8, 8);
         if (e == cudaSuccess) e = orcha::configure_hydro(nd, 16, 8);
@@ -477,13 +489,7 @@ orcha_status orcha_server_destroy(orcha_server* s) {
     }
     for (auto& sl : s->ring) {
         if (sl.ev) cudaEventDestroy(sl.ev);
-        for (auto& g : sl.g) {
-            cudaFree(g.queue_d);
-            cudaFree(g.slots_d);
-            cudaFree(g.items_d);
-            cudaFreeHost(g.slots_pin);
-            cudaFreeHost(g.items_pin);
-        }
+        cudaFreeHost(sl.slots_pin);          // the device arrays live in the pool
     }
     cudaFreeHost(s->res_pin);
     if (s->compute) cudaStreamDestroy(s->compute);
@@ -496,8 +502,10 @@ orcha_status orcha_server_destroy(orcha_server* s) {
 orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, int64_t* ticket) {
     if (!s || !rd || !ticket) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: null argument");
     if (rd->nsteps < 1) return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: nsteps < 1");
-    if (rd->task != ORCHA_TASK_HYDRO_FP64 && rd->task != ORCHA_TASK_HYDRO_F32FLUX && rd->task != ORCHA_TASK_HYDRO_FF)
-        return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: task must be HYDRO_FP64, HYDRO_F32FLUX or HYDRO_FF");
+    if (rd->task != ORCHA_TASK_HYDRO_FP64 && rd->task != ORCHA_TASK_HYDRO_F32FLUX && rd->task != ORCHA_TASK_HYDRO_FF &&
+        rd->task != ORCHA_TASK_HYDRO_F32FLUX_FFSUM)
+        return orcha::set_error(ORCHA_ERR_INVALID,
+                                "server_submit: task must be HYDRO_FP64, HYDRO_F32FLUX, HYDRO_F32FLUX_FFSUM or HYDRO_FF");
     if (rd->init_kind == ORCHA_INIT_FROM_HOST && !rd->init_host)
         return orcha::set_error(ORCHA_ERR_INVALID, "server_submit: FROM_HOST needs init_host");
     if (rd->init_kind == ORCHA_INIT_HALF_SPACE && (rd->region[0] < 0 || rd->region[0] >= rd->ndim))
@@ -531,7 +539,7 @@ orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, 
     r->ty = group_ty(group_of(rd->ndim, r->prec, r->kind));
     r->nitems = (int)r->nblk * (rd->bs[0] / r->tx) * (rd->bs[1] / r->ty);
     r->stats.zone_updates = (int64_t)r->nblk * r->ncell * rd->nsteps;
-    if (r->bytes > s->pool.size) {
+    if (r->bytes > s->pool.size || (size_t)r->nitems > s->cap_items) {
         delete r;
         return orcha::set_error(ORCHA_ERR_OOM, "server_submit: request larger than the whole HBM budget");
     }

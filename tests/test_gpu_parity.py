@@ -59,8 +59,10 @@ def test_sedov_128_packets_of_64_10_steps(oracle_mod):
 
 @pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1), (1, 0, 1)])
 def test_random_jumps_every_tile_shape(oracle_mod, periodic):
-    """Random jumps in every direction (limiter, upwind and fallback branches),
-    two blocks of 16^3 per axis; every tile variant gives the same bits."""
+    """Random jumps in every direction (limiter and upwind branches; at the CFL
+    time step no cell takes the first-order fallback, which
+    tests/test_gpu_fallback.py drives), two blocks of 16^3 per axis; every
+    tile variant gives the same bits."""
     spec = wl.MeshSpec(ndim=3, nb=(2, 2, 2), bs=(16, 16, 16), periodic=periodic)
     U0 = wl.random_blocky_state(spec, 17)
     O, _ = oracle_steps(oracle_mod, spec, U0, 4)
@@ -186,18 +188,23 @@ def test_integer_pipe_conversions_match_hardware():
     assert B.orcha_selftest_conversions(0, 1 << 32, seed=12345) == 0
 
 
-def test_c4_f32flux_100_steps_error_against_fp64_oracle(oracle_mod):
-    """The precision workload: 128^3 Sedov, FP32 reconstruction/flux with the
-    FP64 update, 100 steps. Reports L1(rho) against the FP64 oracle; totals of
-    mass and energy are conserved to 1e-13 (the blast stays inside)."""
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM])
+def test_c4_f32flux_100_steps_error_against_fp64_oracle(oracle_mod, task):
+    """The precision workload: 128^3 Sedov, FP32 reconstruction/flux, 100
+    steps, in the configured arithmetic (face fluxes promoted to FP64 before
+    the difference, FP64 update and signal speed) and in the shortcut (float-
+    float flux sums, FP32 signal speed). Reports L1(rho) against the FP64
+    oracle; totals of mass and energy are conserved to 1e-13 (the blast stays
+    inside)."""
     spec, packets = wl.sedov128_packets(64)
     U0 = wl.sedov_state(spec)
-    G, _, err = gpu_steps(spec, U0, 100, task=B.ORCHA_TASK_HYDRO_F32FLUX, packets=packets)
+    G, _, err = gpu_steps(spec, U0, 100, task=task, packets=packets)
     O, _ = oracle_steps(oracle_mod, spec, U0, 100)
     assert err == 0
     l1 = float(np.abs(G[:, 0] - O[:, 0]).mean())
     l1_rel = l1 / float(np.abs(O[:, 0]).mean())
-    print(f"C4 f32flux 128^3 Sedov, 100 steps: L1(rho) = {l1:.3e} (relative {l1_rel:.3e}), "
+    name = "f32flux" if task == B.ORCHA_TASK_HYDRO_F32FLUX else "f32flux_ffsum"
+    print(f"C4 {name} 128^3 Sedov, 100 steps: L1(rho) = {l1:.3e} (relative {l1_rel:.3e}), "
           f"max |drho| = {np.abs(G[:, 0] - O[:, 0]).max():.3e}")
     assert l1_rel < 1e-5
     for v in (0, 4):
@@ -212,7 +219,7 @@ def test_integer_pipe_fp64_arithmetic_matches_hardware():
 
 
 @pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_FF,
-                                  B.ORCHA_TASK_HYDRO_RK2])
+                                  B.ORCHA_TASK_HYDRO_RK2, B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM])
 @pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1)])
 def test_free_stream_is_preserved_bitwise(task, periodic):
     """A uniform state with an arbitrary velocity is the degenerate case of the

@@ -93,11 +93,12 @@ def test_2d_batch(oracle_mod):
     assert rule12_error(G, O, spec.nvar) <= TOL
 
 
-def test_batch_f32flux_matches_packet_path():
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM])
+def test_batch_f32flux_matches_packet_path(task):
     spec = wl.sedov_spec(64, 16)
     U0 = wl.sedov_state(spec)
-    (G,), _ = gpu_batch_steps([(spec, U0, None)], 5, task=B.ORCHA_TASK_HYDRO_F32FLUX)
-    A, _, _ = gpu_steps(spec, U0, 5, task=B.ORCHA_TASK_HYDRO_F32FLUX)
+    (G,), _ = gpu_batch_steps([(spec, U0, None)], 5, task=task)
+    A, _, _ = gpu_steps(spec, U0, 5, task=task)
     assert np.array_equal(G, A)
 
 
@@ -123,11 +124,12 @@ def test_tail_wave_split_into_z_slabs_keeps_the_bits(tile):
     """512 blocks of 16^3 leave a partial last wave of resident CTAs, whose
     items the batch splits into z slabs (two, or three for the FF variant with
     16x8 tiles on a B300): the result is bitwise the packet path's (every face
-    flux is the same expression whichever item computes it), in all three
-    arithmetic variants."""
+    flux is the same expression whichever item computes it), in every
+    arithmetic variant."""
     spec, packets = wl.sedov128_packets(64)
     U0 = wl.random_blocky_state(spec, 71)
-    for task in (B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_FF):
+    for task in (B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_F32FLUX, B.ORCHA_TASK_HYDRO_FF,
+                 B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM):
         A, _, _ = gpu_steps(spec, U0, 3, packets=packets, task=task)
         (G,), errs = gpu_batch_steps([(spec, U0, packets)], 3, tile=tile, task=task)
         assert errs == [0]

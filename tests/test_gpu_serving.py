@@ -76,10 +76,12 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_mixed_precision_and_block_sizes_in_flight_together():
-    """FP64, FP32-flux and FF requests of block sizes 8, 16 and 32 in flight
-    together: each result equals the same request served alone."""
-    reqs = _requests(9, 5, sizes=(8, 16, 32), max_blocks=4, nsteps=2)
-    tasks = [B.ORCHA_TASK_HYDRO_FP64] * 3 + [B.ORCHA_TASK_HYDRO_F32FLUX] * 3 + [B.ORCHA_TASK_HYDRO_FF] * 3
+    """FP64, FP32-flux (configured and shortcut) and FF requests of block
+    sizes 8, 16 and 32 in flight together: each result equals the same
+    request served alone."""
+    reqs = _requests(12, 5, sizes=(8, 16, 32), max_blocks=4, nsteps=2)
+    tasks = ([B.ORCHA_TASK_HYDRO_FP64] * 3 + [B.ORCHA_TASK_HYDRO_F32FLUX] * 3 + [B.ORCHA_TASK_HYDRO_FF] * 3
+             + [B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM] * 3)
     alone = [_serve([r], task=t)[0][0] for r, t in zip(reqs, tasks)]
     srv = serve.Server(8 << 30)
     try:

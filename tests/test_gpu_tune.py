@@ -27,6 +27,7 @@ def _cuda():
 
 @pytest.mark.parametrize("ndim,bs,task", [(3, (16, 16, 16), B.ORCHA_TASK_HYDRO_FP64),
                                           (3, (8, 8, 8), B.ORCHA_TASK_HYDRO_F32FLUX),
+                                          (3, (16, 16, 16), B.ORCHA_TASK_HYDRO_F32FLUX_FFSUM),
                                           (2, (32, 16, 1), B.ORCHA_TASK_HYDRO_FP64),
                                           (3, (16, 16, 16), B.ORCHA_TASK_HYDRO_FF),
                                           (3, (16, 16, 16), B.ORCHA_TASK_HYDRO_RK2)])
