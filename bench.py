@@ -13,7 +13,8 @@ per-request launches.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload sedov256_uneven|sedov128|sedov128_f32|sedov128_f32x|sedov128_ff|sedov256_uneven_ff|
-                     sedov128_rk2|sedov128_rk2_f32|sedov128_rk2_ff]
+                     sedov128_rk2|sedov128_rk2_f32|sedov128_rk2_ff|sedov128_tb2|sedov128_tb2_f32|
+                     sedov128_rk2_fused|sedov128_rk2_fused_f32]
                     [--no-cpu-baseline] [--no-serving] [--serve-requests N]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
@@ -99,10 +100,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sedov256_uneven",
-                    choices=["sedov128", "sedov128_f32", "sedov128_f32x", "sedov256_uneven", "sedov128_ff",
-                             "sedov256_uneven_ff",
-                             "sedov128_rk2", "sedov128_rk2_f32", "sedov128_rk2_ff"])
+    ap.add_argument("--workload", default="sedov256_uneven", choices=sorted(WORKLOADS))
     ap.add_argument("--tile", default="", choices=["", "8x8", "16x8", "16x16"],
                     help="column tile of the hydro kernel (default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -116,23 +114,35 @@ def parse():
     return ap.parse_args()
 
 
+WORKLOADS = {       # name -> (mesh, task, Heun steps at CFL 0.4)
+    "sedov256_uneven": ("256", "fp64", False), "sedov256_uneven_ff": ("256", "ff", False),
+    "sedov128": ("128", "fp64", False), "sedov128_f32": ("128", "f32flux", False),
+    "sedov128_f32x": ("128", "f32flux_ffsum", False), "sedov128_ff": ("128", "ff", False),
+    "sedov128_rk2": ("128", "rk2", True), "sedov128_rk2_f32": ("128", "rk2_f32", True),
+    "sedov128_rk2_ff": ("128", "rk2_ff", True),
+    "sedov128_tb2": ("128", "tb2", False), "sedov128_tb2_f32": ("128", "tb2_f32", False),
+    "sedov128_rk2_fused": ("128", "rk2_fused", True), "sedov128_rk2_fused_f32": ("128", "rk2_fused_f32", True),
+}
+
+
 def workload(name):
     from paper_2507_09337_b300 import workloads as wl
-    if name.startswith("sedov128"):
+    size, task, rk = WORKLOADS[name]
+    if size == "128":
         spec, packets = wl.sedov128_packets(64)
         desc = "3D Sedov 128^3, 512 blocks of 16^3 + 2 guards, packets of 64, 10 steps"
-        nt = 10
     else:
         spec, packets = wl.sedov256_uneven_packets(0)
         desc = "3D Sedov 256^3, 4096 blocks of 16^3 + 2 guards, packets seed-uniform in [1, 256], 10 steps"
-        nt = 10
-    task = ("f32flux" if name.endswith("_f32") else "f32flux_ffsum" if name.endswith("_f32x")
-            else "ff" if name.endswith("_ff") else "fp64")
-    if "_rk2" in name:
+    nt = 10
+    if rk:
         import dataclasses
-        task = {"fp64": "rk2", "f32flux": "rk2_f32", "ff": "rk2_ff"}[task]
         spec = dataclasses.replace(spec, cfl=0.4)
         desc += "; Heun RK2 steps (two plain-MUSCL stages), CFL 0.4"
+    if task.startswith("tb2"):
+        desc += "; two Hancock steps per launch at the pair's first dt (5 launches)"
+    if "fused" in task:
+        desc += "; both Heun stages in one launch"
     return spec, packets, nt, task, desc
 
 
@@ -140,7 +150,10 @@ DTYPES = {"fp64": "f64", "f32flux": "f32 reconstruction/flux + f64 flux differen
           "f32flux_ffsum": "f32 reconstruction/flux + float-float flux sums + f64 update (f32 signal speed)",
           "ff": "double-word f32x2 reconstruction/flux + f64 update", "rk2": "f64",
           "rk2_f32": "f32 reconstruction/flux + f64 flux differences and update (Heun RK2)",
-          "rk2_ff": "double-word f32x2 reconstruction/flux + f64 update (Heun RK2)"}
+          "rk2_ff": "double-word f32x2 reconstruction/flux + f64 update (Heun RK2)",
+          "tb2": "f64", "tb2_f32": "f32 reconstruction/flux + f64 flux differences, update and signal speed",
+          "rk2_fused": "f64", "rk2_fused_f32": "f32 reconstruction/flux + f64 flux differences and update (Heun RK2)"}
+FTYPES = {"tb2": "rd,false", "tb2_f32": "float,false", "rk2_fused": "rd,true", "rk2_fused_f32": "float,true"}
 KTYPES = {"fp64": "rd", "f32flux": "float", "f32flux_ffsum": "float,false,true", "ff": "dw", "rk2": "rd,true", "rk2_f32": "float,true",
           "rk2_ff": "dw,true"}
 
@@ -348,22 +361,25 @@ def main():
         tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
     batch = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
     hydro_events = []
-    # per bench step: pack, signal speed (one launch), dt reduce, nt persistent launches, unpack
-    launches_per_step = 1 + 1 + 1 + nt * (2 if task_name.startswith("rk2") else 1) + 1
+    # time steps per batch call (a two-step task advances a pair per launch)
+    per_call = 2 if task_name.startswith("tb2") else 1
+    launches_per_call = 2 if task_name in ("rk2", "rk2_f32", "rk2_ff") else 1
+    # per bench step: pack, signal speed (one launch), dt reduce, the hydro launches, unpack
+    launches_per_step = 1 + 1 + 1 + (nt // per_call) * launches_per_call + 1
 
     def step(record: bool):
         B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
         B.orcha_batch_advance(batch, task, 0, True, False, stream)          # dt of the initial state
-        for _ in range(nt):
+        for _ in range(nt // per_call):
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                B.orcha_batch_advance(batch, task, 1, False, False, stream)
+                B.orcha_batch_advance(batch, task, per_call, False, False, stream)
                 e1.record(stream)
-                hydro_events.append((e0, e1, spec.nblocks))
+                hydro_events.append((e0, e1, spec.nblocks * per_call))
             else:
-                B.orcha_batch_advance(batch, task, 1, False, False, stream)
+                B.orcha_batch_advance(batch, task, per_call, False, False, stream)
         B.orcha_mesh_store(h, out_dev.data_ptr(), False, stream)
 
     with torch.cuda.stream(stream):
@@ -405,43 +421,49 @@ def main():
     avg_launch_s = tot_s / len(durs)
     zones_per_launch = tot_zones / len(durs)
     hydro_share = tot_s / (ms * 1e-3)
-    fp64_bound = task_name in ("fp64", "rk2")
+    # per zone update: the roof that bounds the task and its algorithmic
+    # FP64 operations and HBM bytes (a Heun step in two launches moves 200 B,
+    # in one launch 80 B; a two-step launch reads and writes once per pair)
+    ops_zu, bytes_zu = {"rk2": (FLOPS_PER_ZONE_3D_RK2, 200), "rk2_fused": (FLOPS_PER_ZONE_3D_RK2, 80),
+                        "rk2_f32": (0, 200), "rk2_ff": (0, 200), "rk2_fused_f32": (0, 80),
+                        "tb2": (FLOPS_PER_ZONE_3D, 40), "tb2_f32": (0, 40)}.get(task_name, (FLOPS_PER_ZONE_3D, 80))
+    fp64_bound = task_name in ("fp64", "rk2", "rk2_fused", "tb2")
     hbm_peak, hbm_src = 6400.0, "fallback 6.4 TB/s (MEASURED_PEAKS.json absent)"
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
         hbm_src = "measured copy bandwidth (MEASURED_PEAKS.json)"
-    kname = f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>"
+    fused = task_name.startswith("tb2") or "fused" in task_name
+    kname = (f"fused_kernel<3,{tile[0]},{tile[1]},{FTYPES[task_name]}>" if fused else
+             f"persistent_kernel<3,{tile[0]},{tile[1]},{KTYPES[task_name]}>")
     prof = {"sedov128": "persistent_kernel_fp64_sedov128.md",
             "sedov256_uneven": "persistent_kernel_fp64_sedov256.md",
             "sedov128_rk2": "persistent_kernel_rk2_sedov128.md",
             "sedov128_f32": "persistent_kernel_f32flux_sedov128.md",
-            "sedov128_ff": "persistent_kernel_ff_sedov128.md"}.get(args.workload)
+            "sedov128_ff": "persistent_kernel_ff_sedov128.md",
+            "sedov128_tb2_f32": "fused_kernel_sedov128.md", "sedov128_tb2": "fused_kernel_sedov128.md",
+            "sedov128_rk2_fused": "fused_kernel_sedov128.md"}.get(args.workload)
     traffic = profiled_traffic(prof, kname) if prof else None
+    per_launch = {"rk2": "one time step of all packets (two stage launches)",
+                  "rk2_f32": "one time step of all packets (two stage launches)",
+                  "rk2_ff": "one time step of all packets (two stage launches)",
+                  "tb2": "two time steps of all packets", "tb2_f32": "two time steps of all packets"}.get(
+        task_name, "one time step of all packets")
     if fp64_bound:
         # the FP64 pipe bounds this task: its peak is measured here, on this
         # GPU, by the library's FMA throughput probe (lane operations/s)
         fp64_peak = B.orcha_measure_fp64_rate(0) / 1e12
-        flops = FLOPS_PER_ZONE_3D_RK2 if task_name == "rk2" else FLOPS_PER_ZONE_3D
-        achieved = flops * zones_per_launch / avg_launch_s / 1e12
-        # RK2: the recorded traffic is per time step (its two stage launches)
+        achieved = ops_zu * zones_per_launch / avg_launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic,
-                "kernel": kname, "per_launch": "one time step of all packets" + (
-                    " (two stage launches)" if task_name == "rk2" else ""),
-                "ops_per_zone": flops,
+                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": kname, "per_launch": per_launch,
+                "ops_per_zone_update": ops_zu,
                 "peak_source": "measured: FP64 FMA throughput probe (orcha_measure_fp64_rate) on this GPU, "
                                "lane operations/s; the task's operations are counted in the same unit "
                                f"(nominal 2 lanes/SM/clk x 148 SMs x 2032 MHz = {FP64_PEAK_TFLOPS:.3f} T)"}
     else:
-        # a Heun step is two launches: stage 1 reads and writes the state (80 B
-        # per zone), stage 2 also reads the step's initial state (120 B)
-        rk = task_name.startswith("rk2")
-        bytes_per_zone = BYTES_PER_ZONE_3D_RK2_STEP if rk else BYTES_PER_ZONE_3D
-        achieved = bytes_per_zone * zones_per_launch / avg_launch_s / 1e9
+        achieved = bytes_zu * zones_per_launch / avg_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "kernel": kname, "peak_source": hbm_src}
-        if rk:
-            roof["per_launch"] = "one time step of all packets (two stage launches)"
+                "traffic": traffic, "kernel": kname, "peak_source": hbm_src, "per_launch": per_launch,
+                "bytes_per_zone_update": bytes_zu}
     hbm_eff = BYTES_PER_ZONE_3D * value / world / 1e9
     spec_state_mb = mesh.state[0].numel() * 8 / 1e6
 

@@ -29,9 +29,10 @@
  *    synchronises the device except orcha_mesh_poll and the destroy calls.
  *  - Host-detected errors are returned immediately as a negative
  *    orcha_status, with a message in orcha_last_error() (per thread).
- *    Errors found on the device (non-physical state, bounded wait that ran
- *    out) are OR-ed into the mesh's device error word and reported by
- *    orcha_mesh_poll.
+ *    Errors found on the device (non-physical state, a non-finite time
+ *    step, a two-step launch beyond its stability limit) are OR-ed into the
+ *    mesh's device error word and reported by orcha_mesh_poll. No kernel
+ *    waits on another CTA or launch, so none has a timeout.
  *  - Not thread-safe per mesh: calls on one mesh must come from one thread
  *    at a time. Different meshes are independent.
  */
@@ -64,7 +65,7 @@ typedef int32_t orcha_status;
 /* Bits of the device error word (orcha_mesh_poll). */
 #define ORCHA_DEVERR_NONPHYSICAL 1 /* an interior cell had rho <= 0 or p <= 0 (or NaN) */
 #define ORCHA_DEVERR_BAD_DT 2      /* the reduced signal speed was not positive and finite */
-#define ORCHA_DEVERR_TIMEOUT 4     /* a device-side bounded wait gave up */
+#define ORCHA_DEVERR_CFL 8         /* a two-step launch's dt exceeded the second step's stability limit */
 
 /* Initial states (orcha_mesh_init_region, serving requests). FROM_HOST copies
  * host data in. The two
@@ -147,7 +148,26 @@ typedef enum {
      * pressure is not positive); the max-reduction and dt = cfl / max stay
      * FP64, and the first dt uses the same rule. Not in the paper: it moves
      * the per-cell FP64 work off this GPU's scarce FP64 pipe. */
-    ORCHA_TASK_HYDRO_F32FLUX_FFSUM = 14
+    ORCHA_TASK_HYDRO_F32FLUX_FFSUM = 14,
+    /* Batch tasks (orcha_batch_advance only) that apply the operator twice
+     * per persistent launch, with one read and one write of the state for
+     * both: the paper's doubled halo (both Runge-Kutta stages with no guard
+     * refresh between them, the first stage computed redundantly on the
+     * inner halo; section "Experiments", Spark paragraph), here to save the
+     * intermediate state's round trip through HBM. A CTA advances its tile
+     * grown by 2 cells (2 planes in z) into an L2-resident scratch, then the
+     * tile itself from the scratch. Each application gives the bits the
+     * one-step task gives.
+     * TB2: two MUSCL-Hancock steps (as HYDRO_FP64 / HYDRO_F32FLUX) per
+     * launch, both with the dt formed from the state at the start of the
+     * pair (nsteps must be even); the launch checks dt * s(U1) <= 1 for the
+     * intermediate state U1 (the summed-direction rule's stability limit)
+     * and sets ORCHA_DEVERR_CFL otherwise. */
+    ORCHA_TASK_HYDRO_TB2 = 15,
+    ORCHA_TASK_HYDRO_F32FLUX_TB2 = 16,
+    /* One whole Heun step (as HYDRO_RK2 / HYDRO_RK2_F32FLUX) per launch. */
+    ORCHA_TASK_HYDRO_RK2_FUSED = 17,
+    ORCHA_TASK_HYDRO_RK2_F32FLUX_FUSED = 18
 } orcha_task;
 
 /* Mesh geometry and the caller's device buffers. */
@@ -408,7 +428,7 @@ ORCHA_API orcha_status orcha_cfl_dt_noalloc(const orcha_mesh_desc* desc, int32_t
                                             void* stream);
 
 /* Wait for `stream`, then read the device error word into *device_error (0 =
- * none) and clear it. Returns NONFINITE / TIMEOUT when a bit is set. */
+ * none) and clear it. Returns NONFINITE when a bit is set. */
 ORCHA_API orcha_status orcha_mesh_poll(orcha_mesh* mesh, void* stream, int32_t* device_error);
 
 /* Diagnostics: the FP32-flux task converts between binary64 and binary32 on

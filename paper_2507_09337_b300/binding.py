@@ -30,7 +30,7 @@ ORCHA_ERR_UNSUPPORTED = -6
 
 ORCHA_DEVERR_NONPHYSICAL = 1
 ORCHA_DEVERR_BAD_DT = 2
-ORCHA_DEVERR_TIMEOUT = 4
+ORCHA_DEVERR_CFL = 8
 
 ORCHA_TASK_GUARD_FILL = 0
 ORCHA_TASK_HYDRO_FP64 = 1
@@ -47,6 +47,10 @@ ORCHA_TASK_RK2_FF_STAGE1 = 11
 ORCHA_TASK_RK2_FF_STAGE2 = 12
 ORCHA_TASK_HYDRO_RK2_FF = 13
 ORCHA_TASK_HYDRO_F32FLUX_FFSUM = 14
+ORCHA_TASK_HYDRO_TB2 = 15
+ORCHA_TASK_HYDRO_F32FLUX_TB2 = 16
+ORCHA_TASK_HYDRO_RK2_FUSED = 17
+ORCHA_TASK_HYDRO_RK2_F32FLUX_FUSED = 18
 
 ORCHA_INIT_FROM_HOST = 0
 ORCHA_INIT_SPHERE = 1
@@ -54,6 +58,8 @@ ORCHA_INIT_HALF_SPACE = 2
 
 TASKS = {"fp64": ORCHA_TASK_HYDRO_FP64, "f32flux": ORCHA_TASK_HYDRO_F32FLUX, "ff": ORCHA_TASK_HYDRO_FF,
          "f32flux_ffsum": ORCHA_TASK_HYDRO_F32FLUX_FFSUM,
+         "tb2": ORCHA_TASK_HYDRO_TB2, "tb2_f32": ORCHA_TASK_HYDRO_F32FLUX_TB2,
+         "rk2_fused": ORCHA_TASK_HYDRO_RK2_FUSED, "rk2_fused_f32": ORCHA_TASK_HYDRO_RK2_F32FLUX_FUSED,
          "rk2": ORCHA_TASK_HYDRO_RK2, "rk2_f32": ORCHA_TASK_HYDRO_RK2_F32FLUX, "rk2_ff": ORCHA_TASK_HYDRO_RK2_FF}
 
 

@@ -394,6 +394,8 @@ orcha_status orcha_mesh_advance(orcha_mesh* m, orcha_packet* const* pk, int32_t 
     if (!m || (!pk && npk > 0) || npk < 0 || nsteps < 0) return fail(ORCHA_ERR_INVALID, "mesh_advance: bad argument");
     if (!orcha::is_step_task(task))
         return fail(ORCHA_ERR_INVALID, "mesh_advance: task must be a whole-step hydro task");
+    if (orcha::prec_is_fused(orcha::prec_of(task)))
+        return fail(ORCHA_ERR_UNSUPPORTED, "mesh_advance: fused two-application tasks run through orcha_batch_advance");
     long long covered = 0;
     for (int i = 0; i < npk; ++i) {
         if (!pk[i] || pk[i]->mesh != m) return fail(ORCHA_ERR_INVALID, "mesh_advance: packet %d not of this mesh", i);
@@ -446,6 +448,8 @@ orcha_status orcha_batch_destroy(orcha_batch* b) {
         cudaFree(l.items_dev);
         cudaFree(l.slots_dev);
         cudaFree(l.done_dev);
+        cudaFree(l.scratch);
+        cudaFree(l.smax2);
     }
     cudaFree(b->queue);
     cudaFree(b->cur_dev);
@@ -538,13 +542,17 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
     if (prec < 0 || prec >= orcha::kNumPrec) return fail(ORCHA_ERR_INVALID, "batch: not a hydro task variant");
     orcha_batch::List& L = b->lists[prec];
     if (L.built) return ORCHA_OK;
+    const bool fused = orcha::prec_is_fused(prec);
     int per_sm = 0;
-    ORCHA_CUDA(orcha::persistent_occupancy(b->ndim, b->tx, b->ty, prec, &per_sm), "batch occupancy");
+    ORCHA_CUDA(fused ? orcha::fused_occupancy(b->ndim, b->tx, b->ty, prec, &per_sm)
+                     : orcha::persistent_occupancy(b->ndim, b->tx, b->ty, prec, &per_sm),
+               "batch occupancy");
     if (per_sm < 1) return fail(ORCHA_ERR_UNSUPPORTED, "batch: persistent kernel does not fit on an SM");
     const long long G = (long long)per_sm * b->num_sms;
     // z ranges of block columns (3D; a column's planes must fit the 15-bit
-    // fields of Item::zr), else one item per block and tile
-    bool columns = b->ndim == 3;
+    // fields of Item::zr), else one item per block and tile; the fused
+    // variants take whole blocks (their scratch holds one block's planes)
+    bool columns = b->ndim == 3 && !fused;
     for (auto* m : b->meshes) columns = columns && orcha::column_items_fit(m->dev);
     std::vector<orcha::Item> items = columns ? column_items(b, G) : b->base_items;
     const size_t ns = b->meshes.size();
@@ -566,6 +574,24 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
         sl[i].tiles_x = m->dev.bs[0] / b->tx;
         sl[i].tiles_y = m->dev.bs[1] / b->ty;
     }
+    const long long grid = std::min<long long>((long long)items.size(), G);
+    if (fused && e == cudaSuccess) {
+        int bz = 1;
+        for (auto* m : b->meshes) bz = std::max(bz, b->ndim == 3 ? m->dev.bs[2] : 1);
+        L.per_cta = orcha::fused_scratch_doubles(b->ndim, b->tx, b->ty, bz);
+        e = cudaMalloc(&L.scratch, sizeof(double) * (size_t)(L.per_cta * grid));
+        long long nb_all = 0;
+        for (auto* m : b->meshes) nb_all += m->nblk;
+        if (e == cudaSuccess && orcha::prec_is_tb2(prec)) {
+            e = cudaMalloc(&L.smax2, sizeof(unsigned long long) * (size_t)nb_all);
+            if (e == cudaSuccess) e = cudaMemset(L.smax2, 0, sizeof(unsigned long long) * (size_t)nb_all);
+            long long off = 0;
+            for (size_t i = 0; i < ns; ++i) {
+                sl[i].smax2 = L.smax2 + off;
+                off += b->meshes[i]->nblk;
+            }
+        }
+    }
     if (e == cudaSuccess) e = cudaMalloc(&L.slots_dev, sizeof(orcha::SlotDev) * ns);
     if (e == cudaSuccess) e = cudaMalloc(&L.items_dev, sizeof(orcha::Item) * items.size());
     if (e == cudaSuccess) e = cudaMemcpy(L.slots_dev, sl.data(), sizeof(orcha::SlotDev) * ns, cudaMemcpyHostToDevice);
@@ -573,14 +599,31 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
         e = cudaMemcpy(L.items_dev, items.data(), sizeof(orcha::Item) * items.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch work list");
     L.nitems = (int)items.size();
-    L.grid = (int)std::min<long long>((long long)L.nitems, G);
+    L.grid = (int)grid;
     L.built = true;
     return ORCHA_OK;
+}
+
+// Persistent launches that nsteps time steps of `task` take.
+static int batch_launches(orcha_task task, int nsteps) {
+    const int prec = orcha::prec_of(task);
+    if (orcha::prec_is_tb2(prec)) return nsteps / 2;       // two steps per launch
+    if (orcha::prec_is_fused(prec)) return nsteps;         // a whole Heun step per launch
+    return nsteps * (orcha::is_rk_step_task(task) ? 2 : 1);
 }
 
 static orcha_status enqueue_batch_steps(orcha_batch* b, orcha_task task, int nsteps, cudaStream_t st) {
     const int prec = orcha::prec_of(task);
     const orcha_batch::List& L = b->lists[prec];
+    if (orcha::prec_is_fused(prec)) {
+        for (int n = 0; n < batch_launches(task, nsteps); ++n) {
+            ORCHA_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(unsigned), st), "batch queue reset");
+            ORCHA_CUDA(orcha::launch_fused(b->ndim, b->tx, b->ty, prec, L.slots_dev, L.items_dev, L.nitems, b->queue,
+                                           L.scratch, L.per_cta, L.grid, st),
+                       "batch fused launch");
+        }
+        return ORCHA_OK;
+    }
     const int stages = orcha::is_rk_step_task(task) ? 2 : 1;     // a Heun step is two launches
     for (int n = 0; n < nsteps; ++n) {
         for (int k = 1; k <= stages; ++k) {
@@ -598,6 +641,8 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
     if (!b || nsteps < 0) return fail(ORCHA_ERR_INVALID, "batch_advance: bad argument");
     if (!orcha::is_step_task(task))
         return fail(ORCHA_ERR_INVALID, "batch_advance: task must be a whole-step hydro task");
+    if (orcha::prec_is_tb2(orcha::prec_of(task)) && nsteps % 2)
+        return fail(ORCHA_ERR_INVALID, "batch_advance: a two-step task needs an even nsteps");
     cudaStream_t st = (cudaStream_t)stream;
     orcha_status s;
     if ((s = ensure_list(b, orcha::prec_of(task)))) return s;
@@ -637,7 +682,7 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
         }
         ORCHA_CUDA(cudaGraphLaunch(exec, st), "batch graph launch");
     }
-    const int flips = nsteps * (orcha::is_rk_step_task(task) ? 2 : 1);     // one per launch
+    const int flips = batch_launches(task, nsteps);     // one per launch
     for (auto* m : b->meshes) m->cur ^= (flips & 1);
     return ORCHA_OK;
 }
@@ -650,8 +695,10 @@ orcha_status orcha_mesh_poll(orcha_mesh* m, void* stream, int32_t* device_error)
     ORCHA_CUDA(cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost), "mesh_poll read");
     ORCHA_CUDA(cudaMemset(m->err, 0, sizeof(int)), "mesh_poll clear");
     *device_error = h;
-    if (h & ORCHA_DEVERR_TIMEOUT) return fail(ORCHA_ERR_TIMEOUT, "device wait timed out (error word %d)", h);
-    if (h) return fail(ORCHA_ERR_NONFINITE, "device reported a non-physical state (error word %d)", h);
+    if (h)
+        return fail(ORCHA_ERR_NONFINITE,
+                    "device error word %d (1 non-physical state, 2 non-finite dt, 8 two-step launch beyond its "
+                    "stability limit)", h);
     return ORCHA_OK;
 }
 

@@ -287,6 +287,45 @@ struct Tile {
     }
 };
 
+// Where a hydro_tile sweep reads its planes and where its new state goes.
+// GlobalIO is the one-step task: planes gathered from the state buffer Uin,
+// new values written into the interiors of Uout, signal speeds raised. The
+// two passes of a fused sweep (fused.cuh) keep the intermediate state of an
+// extended tile in a per-CTA scratch instead:
+//   pass A (ScratchOutIO): the tile grown by 2 cells on each side in x and
+//     y, and by 2 planes in z (x0, y0, z0 lowered by 2, z1 raised by 2);
+//     planes from Uin, base values gathered from Uin as well (owner columns
+//     can lie in neighbouring blocks), new values into
+//     scratch[plane - z0][var][column of the grown tile];
+//   pass B (ScratchInIO): the tile itself; planes and base values from the
+//     scratch (positions beyond an outflow edge of the domain read the
+//     nearest in-domain cell, the boundary rule), new values into Uout; a
+//     Heun second stage averages with the step's initial state in Uin.
+// kThreads: the CTA size of a fused launch (pass A's thread count); a pass
+// with fewer threads idles the rest outside its barriers.
+struct GlobalIO {
+    static constexpr bool kIn = false;      // planes and base values from the scratch
+    static constexpr bool kOut = false;     // new values into the scratch
+    static constexpr int kRaise = 1;        // 0: none; 1: m.smax (RK: stage 2); 2: the inner cells into io.smax2
+    static constexpr int kThreads = 0;      // 0: the variant's own thread count
+    double* scratch = nullptr;
+    unsigned long long* smax2 = nullptr;    // kRaise 2: per-block maxima of the intermediate state
+};
+template <int NTH, int RAISE>
+struct ScratchOutIO {
+    static constexpr bool kIn = false, kOut = true;
+    static constexpr int kRaise = RAISE, kThreads = NTH;
+    double* scratch;
+    unsigned long long* smax2;
+};
+template <int NTH>
+struct ScratchInIO {
+    static constexpr bool kIn = true, kOut = false;
+    static constexpr int kRaise = 1, kThreads = NTH;
+    double* scratch;
+    unsigned long long* smax2;
+};
+
 // One column tile of one block: the z sweep over interior planes [z0, z1)
 // (default: the whole block; a sub-range recomputes its own z halo, so a
 // block may be advanced as several z slabs with the same result bits). With
@@ -313,11 +352,11 @@ struct Tile {
 // update and the new state's signal speed are FP64, as for T = rd. With FX
 // the differences are formed exactly in float-float, summed to ~46 bits, and
 // the signal speed is evaluated in FP32 (rounded up by 1 + 2^-18).
-template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false, bool FX = false>
+template <int NDIM, int TX, int TY, class T, bool GATHER, bool RK = false, bool FX = false, class IO = GlobalIO>
 __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, const int x0, const int y0,
                                            const double* __restrict__ Uin, double* __restrict__ Uout,
                                            unsigned char* smem_raw, unsigned long long* red, int z0 = 0,
-                                           int z1 = -1, int stage = 0) {
+                                           int z1 = -1, int stage = 0, IO io = IO{}) {
     using Tl = Tile<NDIM, TX, TY>;
     using S = typename P<T>::store;
     constexpr int NV = Tl::NV, NW = Tl::NW, NT = Tl::NT;
@@ -357,7 +396,10 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     // their own cell; every thread loads planes and forms face fluxes.
     constexpr int NB = Tl::template nb<T, RK>();
     constexpr bool kSplit = NB > NT;
-    const bool owner = !kSplit || tid < NT;
+    static_assert(IO::kThreads == 0 || IO::kThreads >= NB, "a fused launch has at least each pass's threads");
+    constexpr bool kPartial = IO::kThreads > NB;     // threads NB.. only take part in the barriers
+    const bool member = !kPartial || tid < NB;
+    const bool owner = kPartial ? tid < NT : (!kSplit || tid < NT);
     const int ti = tid % TX, tj = tid / TX;         // owner column
     const int o2 = (tj + 2) * R2X + (ti + 2);       // in the R2 plane
     const int o1 = (tj + 1) * R1X + (ti + 1);       // in the R1 plane
@@ -417,12 +459,60 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             }
             bxy[k][e] = sbx + m.nb[0] * sby;
             oxy[k][e] = sy * px + sx;
+            if constexpr (IO::kIn) {
+                // the scratch holds this tile's R2 cells; beyond an outflow
+                // edge of the domain the boundary rule's cell is read instead
+                int cc[2] = {ci, cj};
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const int n = m.nb[d] * m.bs[d];
+                    const int gi = bc[d] * m.bs[d] + (d == 0 ? x0 : y0) + cc[d] - kGuard;
+                    if (!m.periodic[d]) cc[d] -= gi < 0 ? gi : (gi > n - 1 ? gi - (n - 1) : 0);
+                }
+                bxy[k][e] = 0;
+                oxy[k][e] = cc[1] * R2X + cc[0];
+            }
             if (ci >= 2 && ci < TX + 2 && cj >= 2 && cj < TY + 2) interior_mask |= 1u << (2 * k + e);
         }
         if (bxy[k][1] == bxy[k][0] && oxy[k][1] == oxy[k][0] + 1) contig_mask |= 1u << k;
     }
     const int nbxy = m.nb[0] * m.nb[1];
     const int plane = py * px;
+    // pass A of a fused sweep: the source of the owner's own column (for its
+    // base values), gathered like the loads (it may lie in a neighbour block)
+    int own_b = 0, own_o = 0;
+    if constexpr (IO::kOut) {
+        const int l[2] = {x0 + ti, y0 + tj};
+        int sb[2], sl[2];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const int n = m.nb[d] * m.bs[d];
+            int gi = bc[d] * m.bs[d] + l[d];
+            if (m.periodic[d]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+            else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
+            sb[d] = gi / m.bs[d];
+            sl[d] = gi % m.bs[d] + kGuard;
+        }
+        own_b = sb[0] + m.nb[0] * sb[1];
+        own_o = sl[1] * px + sl[0];
+    }
+    // plane pzi's slot in the scratch of a fused sweep (pass A writes planes
+    // z0 .. z1-1 of its grown range, pass B reads z0-2 .. z1+1 of its own)
+    auto scratch_slot = [&](int pzi) -> int {
+        if (NDIM != 3) return 0;
+        if constexpr (IO::kIn) {
+            if (!m.periodic[2]) {        // beyond an outflow edge: the boundary plane
+                const int n = m.nb[2] * m.bs[2], gz = bc[2] * m.bs[2] + pzi;
+                pzi -= gz < 0 ? gz : (gz > n - 1 ? gz - (n - 1) : 0);
+            }
+            return pzi - (z0 - 2);
+        }
+        return pzi - z0;
+    };
+    const long long lvs = IO::kIn ? (long long)R2N : vs;   // variable stride of the plane source
+    // slot of plane pzi in the three-plane ring; planes run from -2 (from -4
+    // in pass A of a fused sweep), and % of a negative number is negative
+    auto ring_slot = [](int pzi) -> int { return (pzi + 6) % 3; };
 
     // z part of the source of plane pzi (interior z index, -2 .. bz+1; 2D: 0):
     // the block-index offset (zb) and the in-block cell offset (zc)
@@ -430,6 +520,10 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         zb = 0;
         zc = 0;
         if (NDIM != 3) return;
+        if constexpr (IO::kIn) {
+            zc = scratch_slot(pzi) * NV * R2N;
+            return;
+        }
         int sbz = bc[2], sz = pzi + kGuard;
         if (GATHER && (pzi < 0 || pzi >= bz)) {
             const int n = m.nb[2] * m.bs[2];
@@ -444,6 +538,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     };
     // source of cell e of pair k of this thread in the plane with z part (zb, zc)
     auto src_of = [&](int k, int e, int zb, int zc) -> const double* {
+        if constexpr (IO::kIn) return io.scratch + (oxy[k][e] + zc);
         return Uin + (long long)(bxy[k][e] + zb) * m.blk_stride + (oxy[k][e] + zc);
     };
     // Ask L2 for the source lines of plane pzi ahead of its load (no registers held).
@@ -452,19 +547,19 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         plane_z(pzi, zb, zc);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (tid + k * NB >= R2P) break;
+            if (tid + k * NB >= R2P || !member) break;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 if (e == 1 && ((contig_mask >> k) & 1u)) break;     // same 16 bytes as cell 0
                 const double* src = src_of(k, e, zb, zc);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + v * vs));
+                for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + v * lvs));
             }
         }
     };
     // L: primitives of plane pzi into its ring slot
     auto load_plane = [&](int pzi) {
-        const int slot = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
+        const int slot = (NDIM == 3) ? ring_slot(pzi) : 0;
         S* w = sW + slot * NW * R2N;
         int zb, zc;
         plane_z(pzi, zb, zc);
@@ -472,13 +567,13 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int q = tid + k * NB;
-            if (q >= R2P) break;
+            if (q >= R2P || !member) break;
             double u[2][NV];
             const double* s0 = src_of(k, 0, zb, zc);
             if (((contig_mask >> k) & 1u) && ((reinterpret_cast<uintptr_t>(s0) & 15u) == 0)) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const double2 d = *reinterpret_cast<const double2*>(s0 + v * vs);
+                    const double2 d = *reinterpret_cast<const double2*>(s0 + v * lvs);
                     u[0][v] = d.x;
                     u[1][v] = d.y;
                 }
@@ -486,8 +581,8 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                 const double* s1 = src_of(k, 1, zb, zc);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    u[0][v] = s0[v * vs];
-                    u[1][v] = s1[v * vs];
+                    u[0][v] = s0[v * lvs];
+                    u[1][v] = s1[v * lvs];
                 }
             }
             if constexpr (std::is_same<T, float>::value) {
@@ -533,7 +628,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     using A2 = Arith<T, 2>;      // arithmetic type of the predictor
     auto predict_core = [&](int pzi, int c2, A2 (&Wc)[NV], A2 (&dW)[3][NV], A2 (&Wb)[NV]) {
         using A = A2;
-        const int sc = (NDIM == 3) ? ((pzi + 3) % 3) : 0;
+        const int sc = (NDIM == 3) ? ring_slot(pzi) : 0;
         const S* w = sW + sc * NW * R2N;
 #pragma unroll
         for (int v = 0; v < NV; ++v) Wc[v] = as<A>(P<T>::ld(&w[v * R2N + c2]));
@@ -546,8 +641,8 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             if (d == 0) { cm = c2 - 1; cp = c2 + 1; wm = w; wp = w; }
             else if (d == 1) { cm = c2 - R2X; cp = c2 + R2X; wm = w; wp = w; }
             else {
-                wm = sW + ((pzi + 2) % 3) * NW * R2N;     // plane pzi-1
-                wp = sW + ((pzi + 4) % 3) * NW * R2N;     // plane pzi+1
+                wm = sW + ring_slot(pzi - 1) * NW * R2N;
+                wp = sW + ring_slot(pzi + 1) * NW * R2N;
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -696,6 +791,29 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         cl[d] = F32 ? d2f_rn(__dsub_rn(cd[d], to_f64(ch[d]))) : 0.0f;
     }
 
+    // base value of the owner's cell of plane q (gi: its offset in the block
+    // column, GlobalIO), where its new value goes, and whether its signal
+    // speed counts (see the IO policies)
+    auto cell_base = [&](int q, long long gi) -> const double* {
+        if constexpr (IO::kIn) return io.scratch + (long long)scratch_slot(q) * NV * R2N + o2;
+        if constexpr (IO::kOut) {
+            int zb, zc;
+            plane_z(q, zb, zc);
+            return Uin + (long long)(own_b + zb) * m.blk_stride + (own_o + zc);
+        }
+        return Ub + gi;
+    };
+    auto store_new = [&](int q, long long gi, int v, double x) {
+        if constexpr (IO::kOut) io.scratch[((long long)scratch_slot(q) * NV + v) * NT + tid] = x;
+        else Ob[gi + v * vs] = x;
+    };
+    auto raise_here = [&](int q) -> bool {
+        if constexpr (IO::kRaise == 1) return !RK || stage == 2;
+        if constexpr (IO::kRaise == 2)        // the fused item's own cells, not its halo
+            return ti >= 2 && ti < TX - 2 && tj >= 2 && tj < TY - 2 && (NDIM != 3 || (q >= z0 + 2 && q < z1 - 2));
+        return false;
+    };
+
     const int pbeg = (NDIM == 3) ? z0 - 1 : 0, pend = (NDIM == 3) ? z1 : 0;
     if (NDIM == 3) {
         if (Prefetch<T>::value) { prefetch_plane(z0 - 1); prefetch_plane(z0); }
@@ -744,7 +862,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
         // ---- F: x and y face fluxes of plane p
         if (inner) {
-            for (int f = tid; f < Tl::NXF + Tl::NYF; f += NB) {
+            for (int f = member ? tid : Tl::NXF + Tl::NYF; f < Tl::NXF + Tl::NYF; f += NB) {
                 int iL, iR, fL, fR, nrm;
                 if (f < Tl::NXF) {
                     const int fi = f % (TX + 1), fj = f / (TX + 1);
@@ -797,29 +915,31 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                 if (owner) {
                     const long long gi = (long long)qb * nbxy * m.blk_stride +
                                          ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                    const double* ub = cell_base(q, gi);
+                    const long long bvs = IO::kIn ? (long long)R2N : vs;
                     rd Un[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         if constexpr (F32) {
                             const ff tz = ff_scale(ff_diff(Fz[v], Fz_prev[v]), ch[2], cl[2]);
-                            Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
+                            Un[v] = rd(ub[v * bvs]) - rd(ff_to_double(ff_add(acc_ff[v], tz)));
                         } else if constexpr (DW) {
                             const dw tz = cdw[2] * (Fz[v] - Fz_prev[v]);
-                            Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
+                            Un[v] = rd(ub[v * bvs]) - rd(P<dw>::to_double(acc_dw[v] + tz));
                         } else {
                             const rd acc = rd(acc_prev[v]) +
                                            rd(cd[2]) * (rd(P<T>::to_double(Fz[v])) - rd(P<T>::to_double(Fz_prev[v])));
-                            Un[v] = rd(Ub[gi + v * vs]) - acc;
+                            Un[v] = rd(ub[v * bvs]) - acc;
                         }
                         // Heun stage 2: the average with the step's initial state, in FP64
-                        if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
-                        Ob[gi + v * vs] = Un[v].v;
+                        if (RK && stage == 2) Un[v] = P<rd>::half(rd((IO::kIn ? Ub : Ob)[gi + v * vs]) + Un[v]);
+                        store_new(q, gi, v, Un[v].v);
                     }
-                    if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
+                    if (raise_here(q)) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
                 }
                 // leaving a block (or the item's range): raise its signal speed
                 // (CTA-uniform: every thread takes part, non-owners with 0)
-                if ((!RK || stage == 2) && (q == z1 - 1 || ql == bz - 1)) {
+                if (IO::kRaise == 1 && (!RK || stage == 2) && (q == z1 - 1 || ql == bz - 1)) {
                     cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
                     smaxb = 0ull;
                 }
@@ -852,22 +972,26 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             }
             if (NDIM == 2) {
                 const long long gi = ((long long)(y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
+                const double* ub = cell_base(0, gi);
+                const long long bvs = IO::kIn ? (long long)R2N : vs;
                 rd Un[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    if constexpr (F32) Un[v] = rd(Ub[gi + v * vs]) - rd(ff_to_double(acc_ff[v]));
-                    else if constexpr (DW) Un[v] = rd(Ub[gi + v * vs]) - rd(P<dw>::to_double(acc_dw[v]));
-                    else Un[v] = rd(Ub[gi + v * vs]) - rd(acc_prev[v]);
-                    if (RK && stage == 2) Un[v] = P<rd>::half(rd(Ob[gi + v * vs]) + Un[v]);
-                    Ob[gi + v * vs] = Un[v].v;
+                    if constexpr (F32) Un[v] = rd(ub[v * bvs]) - rd(ff_to_double(acc_ff[v]));
+                    else if constexpr (DW) Un[v] = rd(ub[v * bvs]) - rd(P<dw>::to_double(acc_dw[v]));
+                    else Un[v] = rd(ub[v * bvs]) - rd(acc_prev[v]);
+                    if (RK && stage == 2) Un[v] = P<rd>::half(rd((IO::kIn ? Ub : Ob)[gi + v * vs]) + Un[v]);
+                    store_new(0, gi, v, Un[v].v);
                 }
-                if (!RK || stage == 2) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
+                if (raise_here(0)) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
             }
         }
     }
     if constexpr (NDIM == 2) {
-        if (!RK || stage == 2) cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
+        if (IO::kRaise == 1 && (!RK || stage == 2))
+            cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
     }
+    if constexpr (IO::kRaise == 2) cta_raise_smax(__longlong_as_double((long long)smaxb), red, &io.smax2[blk]);
 }
 
 // Packet path: one CTA per (packet block, column tile); guards come from the

@@ -14,13 +14,20 @@ namespace orcha {
 // FP64 update), and Heun Runge-Kutta stages (plain MUSCL) in the same three
 // arithmetics.
 // kF32X: the FP32-flux shortcut (float-float flux sums, FP32 signal speed).
-enum Prec : int { kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3, kRK2F32 = 4, kRK2FF = 5, kF32X = 6 };
-constexpr int kNumPrec = 7;
+// kTB2, kTB2F32: two Hancock steps per launch (FP64, FP32 flux); kFRK2,
+// kFRK2F32: both Heun stages in one launch (fused.cuh).
+enum Prec : int {
+    kF64 = 0, kF32 = 1, kFF = 2, kRK2 = 3, kRK2F32 = 4, kRK2FF = 5, kF32X = 6,
+    kTB2 = 7, kTB2F32 = 8, kFRK2 = 9, kFRK2F32 = 10
+};
+constexpr int kNumPrec = 11;
 inline bool prec_is_rk(int p) { return p == kRK2 || p == kRK2F32 || p == kRK2FF; }
+inline bool prec_is_fused(int p) { return p >= kTB2; }
+inline bool prec_is_tb2(int p) { return p == kTB2 || p == kTB2F32; }
 // variants whose first dt uses the FP32 signal-speed rule (the shortcut's)
 inline bool prec_f32_dt(int p) { return p == kF32X; }
 // variants with FP32 reconstruction and fluxes
-inline bool prec_is_f32(int p) { return p == kF32 || p == kF32X || p == kRK2F32; }
+inline bool prec_is_f32(int p) { return p == kF32 || p == kF32X || p == kRK2F32 || p == kTB2F32 || p == kFRK2F32; }
 inline bool prec_is_dw(int p) { return p == kFF || p == kRK2FF; }
 // Variant of a hydro task, or -1 for any other task.
 inline int prec_of(orcha_task t) {
@@ -28,6 +35,10 @@ inline int prec_of(orcha_task t) {
         case ORCHA_TASK_HYDRO_FP64: return kF64;
         case ORCHA_TASK_HYDRO_F32FLUX: return kF32;
         case ORCHA_TASK_HYDRO_F32FLUX_FFSUM: return kF32X;
+        case ORCHA_TASK_HYDRO_TB2: return kTB2;
+        case ORCHA_TASK_HYDRO_F32FLUX_TB2: return kTB2F32;
+        case ORCHA_TASK_HYDRO_RK2_FUSED: return kFRK2;
+        case ORCHA_TASK_HYDRO_RK2_F32FLUX_FUSED: return kFRK2F32;
         case ORCHA_TASK_HYDRO_FF: return kFF;
         case ORCHA_TASK_HYDRO_RK2:
         case ORCHA_TASK_RK2_STAGE1:
@@ -66,7 +77,7 @@ inline orcha_task rk_stage_task(orcha_task step, int k) {
 // Tasks that advance whole steps (mesh_advance, batch_advance, autotune).
 inline bool is_step_task(orcha_task t) {
     return t == ORCHA_TASK_HYDRO_FP64 || t == ORCHA_TASK_HYDRO_F32FLUX || t == ORCHA_TASK_HYDRO_FF ||
-           t == ORCHA_TASK_HYDRO_F32FLUX_FFSUM ||
+           t == ORCHA_TASK_HYDRO_F32FLUX_FFSUM || prec_is_fused(prec_of(t)) ||
            is_rk_step_task(t);
 }
 
@@ -127,6 +138,15 @@ cudaError_t launch_persistent(int ndim, int tx, int ty, int prec, const SlotDev*
 // Full-block items of slots[0..nslots) written at items[slot.item0 ...]
 // (block-major, tile-minor), so a caller uploads only the slots.
 cudaError_t launch_expand_items(const SlotDev* slots, int nslots, Item* items, cudaStream_t st);
+// Fused two-application launches (prec kTB2 .. kFRK2F32, fused.cuh): one
+// launch advances every mesh of `slots` by two Hancock steps or one whole
+// Heun step; scratch holds per_cta doubles per resident CTA (grid CTAs).
+cudaError_t launch_fused(int ndim, int tx, int ty, int prec, const SlotDev* slots, const Item* items, int nitems,
+                         unsigned* queue, double* scratch, long long per_cta, int grid, cudaStream_t st);
+cudaError_t fused_occupancy(int ndim, int tx, int ty, int prec, int* per_sm);
+cudaError_t configure_fused(int ndim, int tx, int ty, int prec);
+// Scratch doubles of one fused CTA for blocks of bz planes.
+long long fused_scratch_doubles(int ndim, int tx, int ty, int bz);
 // Resident CTAs per SM of a persistent variant.
 cudaError_t persistent_occupancy(int ndim, int tx, int ty, int prec, int* per_sm);
 

@@ -33,6 +33,7 @@ struct SlotDev {
     int nblk;
     int tiles_x, tiles_y;
     int item0;              // position of this mesh's first item (full-block items built on the device)
+    unsigned long long* smax2;  // two-step launches: per-block signal speed of the intermediate state (else null)
 };
 
 // One unit of work: a column tile of block blk over its interior planes, or,
@@ -46,17 +47,37 @@ struct Item {
 // false: the first stage of a Runge-Kutta step keeps dt), clear the maxima
 // and the item counter, flip the current buffer. Called by all threads of
 // one CTA.
-__device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red, bool update_dt) {
+// Largest of a per-block maximum array over the CTA (all threads call it;
+// thread 0 gets the result).
+__device__ __forceinline__ unsigned long long cta_max_of(const unsigned long long* a, int n, unsigned long long* red) {
     unsigned long long b = 0;
-    for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) b = umax64(b, __ldcg(&sd.m.smax[i]));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) b = umax64(b, __ldcg(&a[i]));
     b = warp_max_u64(b);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t = umax64(t, red[w]);
+    __syncthreads();
+    return t;
+}
+
+// Finish a mesh's step: dt = cfl / max signal speed (unless update_dt is
+// false: the first stage of a Runge-Kutta step keeps dt), clear the maxima
+// and the item counter, flip the current buffer. A two-step launch (smax2
+// set) also checks that its shared dt kept the second step stable:
+// dt * s(intermediate state) <= 1, the limit of the summed-direction rule,
+// else ORCHA_DEVERR_CFL. Called by all threads of one CTA.
+__device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red, bool update_dt) {
+    const unsigned long long t = cta_max_of(sd.m.smax, sd.nblk, red);
+    const unsigned long long t2 = sd.smax2 ? cta_max_of(sd.smax2, sd.nblk, red) : 0ull;
+    if (threadIdx.x == 0) {
         const double s = __longlong_as_double((long long)t);
+        if (sd.smax2) {
+            const double s1 = __longlong_as_double((long long)t2);
+            if (!(s1 >= 0.0 && *sd.dt * s1 <= 1.0)) atomicOr(sd.m.err, 8);
+        }
         if (update_dt) {
             if (s > 0.0 && s <= 1.7976931348623157e308) *sd.dt = sd.m.cfl / s;
             else atomicOr(sd.m.err, 2);
@@ -65,6 +86,8 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
         *sd.cur ^= 1;
     }
     for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.m.smax[i] = 0ull;
+    if (sd.smax2)
+        for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.smax2[i] = 0ull;
 }
 
 // Resident CTAs per SM requested from the register allocator (A/B-measured

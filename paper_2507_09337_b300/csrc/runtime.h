@@ -55,6 +55,9 @@ struct orcha_batch {
         orcha::Item* items_dev = nullptr;
         orcha::SlotDev* slots_dev = nullptr;
         unsigned* done_dev = nullptr;
+        double* scratch = nullptr;                   // fused variants: per-CTA intermediate state
+        long long per_cta = 0;                       // its doubles per CTA
+        unsigned long long* smax2 = nullptr;         // two-step variants: intermediate state's block speeds
     } lists[orcha::kNumPrec];                        // indexed by orcha::Prec
     unsigned* queue = nullptr;
     int* cur_dev = nullptr;

@@ -133,7 +133,9 @@ extern "C" orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_
             if (e != cudaSuccess) { s = orcha::cuda_error(e, "autotune: state"); break; }
             orcha_batch* b = nullptr;
             if ((s = orcha_batch_create(&pk, 1, t[0], t[1], &b))) break;
-            const int warm = 2, steps = 5;
+            // two-step launches need even step counts
+            const bool pairs = orcha::prec_is_tb2(orcha::prec_of(task));
+            const int warm = 2, steps = pairs ? 6 : 5;
             s = orcha_batch_advance(b, task, warm, 1, 0, st);
             if (!s) e = cudaEventRecord(e0, st);
             if (!s && e == cudaSuccess) s = orcha_batch_advance(b, task, steps, 0, 0, st);

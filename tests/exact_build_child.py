@@ -13,7 +13,7 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 from paper_2507_09337_b300 import binding as B  # noqa: E402
 from paper_2507_09337_b300 import workloads as wl  # noqa: E402
-from tests.gpu_helpers import gpu_batch_steps, gpu_one_step, gpu_steps, oracle_steps  # noqa: E402
+from tests.gpu_helpers import gpu_batch_fixed_dt, gpu_batch_steps, gpu_one_step, gpu_steps, oracle_steps  # noqa: E402
 
 
 def main():
@@ -56,6 +56,27 @@ def main():
                 G = gpu_one_step(spec, U0, step_dt, B.ORCHA_TASK_HYDRO_FP64, tile, path)
                 res[f"{path}_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(G, O))
         print(json.dumps(res), flush=True)
+    # two operator applications per launch: two Hancock steps at one dt, and
+    # a whole Heun step
+    import dataclasses
+    U2 = wl.random_blocky_state(jumps, 17)
+    m = oracle.Mesh(**jumps.oracle_kwargs())
+    dt = oracle.dt(m, U2)
+    O1, _, _ = oracle.step(m, U2, dt)
+    O2, _, _ = oracle.step(m, O1, dt)
+    rk = dataclasses.replace(jumps, cfl=0.4)
+    mr = oracle.Mesh(**rk.oracle_kwargs())
+    dtr = oracle.dt(mr, U2)
+    OR, _, _ = oracle.step_rk2(mr, U2, dtr)
+    res_tb = {"case": "tb2"}
+    res_rk = {"case": "rk2_fused"}
+    for tile in [(8, 8), (16, 8), (16, 16)]:
+        G, err, _ = gpu_batch_fixed_dt(jumps, U2, dt, B.ORCHA_TASK_HYDRO_TB2, tile, 2)
+        res_tb[f"batch_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(G, O2)) and err == 0
+        G, err, _ = gpu_batch_fixed_dt(rk, U2, dtr, B.ORCHA_TASK_HYDRO_RK2_FUSED, tile, 1)
+        res_rk[f"batch_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(G, OR)) and err == 0
+    print(json.dumps(res_tb), flush=True)
+    print(json.dumps(res_rk), flush=True)
 
 
 if __name__ == "__main__":

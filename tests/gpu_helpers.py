@@ -97,10 +97,12 @@ def gpu_batch_steps(problems, nsteps, task=B.ORCHA_TASK_HYDRO_FP64, tile=(0, 0),
 
 
 def _poll(mesh, stream=None):
-    try:
-        return mesh.poll(stream)
-    except B.OrchaError:
-        return -1
+    """Wait for the stream, then read and clear the mesh's device error word
+    (returned, not raised)."""
+    import ctypes
+    word = ctypes.c_int32()
+    B.lib().orcha_mesh_poll(mesh.handle, B._stream_ptr(stream), ctypes.byref(word))
+    return word.value
 
 
 def gpu_one_step(spec, U0, dt, task, tile, path):
@@ -134,6 +136,28 @@ def gpu_one_step(spec, U0, dt, task, tile, path):
             B.orcha_batch_advance(batch, task, 1, False, False, s)
             _poll(mesh, s)
         return mesh.store()
+    finally:
+        if batch:
+            B.orcha_batch_destroy(batch)
+        mesh.close()
+
+
+def gpu_batch_fixed_dt(spec, U0, dt, task, tile, nsteps):
+    """nsteps steps of a batch task starting from the time step dt (written
+    into dt_dev; init_dt = 0). Returns (state, device error word, dt_dev
+    after the run)."""
+    import torch
+    mesh = B.Mesh(spec)
+    batch = None
+    try:
+        mesh.load(U0)
+        mesh.dt.fill_(dt)
+        batch = B.orcha_batch_create(mesh.packets, *tile)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        B.orcha_batch_advance(batch, task, nsteps, False, False, s)
+        err = _poll(mesh, s)
+        return mesh.store(), err, mesh.dt_value()
     finally:
         if batch:
             B.orcha_batch_destroy(batch)
