@@ -9,7 +9,8 @@ scheme's arithmetic.
 Contents:
   * ``oracle.c`` -- the scheme as plain per-block loops (see its header);
     wrapped here by :func:`step`, :func:`step_rk2`, :func:`stage`, :func:`dt`,
-    :func:`run`, :func:`hll`, :func:`minmod`. Pinned by tests/test_oracle_pins.py (exact Sod solution,
+    :func:`run`, :func:`hll`, :func:`minmod`, and the two-level AMR step
+    :func:`amr_step` / :func:`amr_dt` / :func:`amr_run`. Pinned by tests/test_oracle_pins.py (exact Sod solution,
     Sedov radius, conservation, symmetries, free stream, closed-form dt,
     convergence order) and tests/test_oracle_mutations.py (planted mistakes
     are caught).
@@ -62,6 +63,13 @@ def _declare(L):
     L.ora_step_rk2.restype = ctypes.c_long
     L.ora_run_scheme.argtypes = [mp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
     L.ora_run_scheme.restype = ctypes.c_int
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.ora_amr_step.argtypes = [mp, ip, ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
+    L.ora_amr_step.restype = ctypes.c_long
+    L.ora_amr_dt.argtypes = [mp, ip, ctypes.c_int, dp, dp]
+    L.ora_amr_dt.restype = ctypes.c_double
+    L.ora_amr_max_signal_speed.argtypes = [mp, ip, ctypes.c_int, dp, dp]
+    L.ora_amr_max_signal_speed.restype = ctypes.c_double
     L.ora_set_threads.argtypes = [ctypes.c_int]
     L.ora_set_threads.restype = None
     L.ora_get_threads.argtypes = []
@@ -239,6 +247,52 @@ class Variant:
         return U, dts[:nsteps], bf
 
 
+    # ---------------------------------------------------------------- two-level AMR
+    def _amr_args(self, mesh: Mesh, refined, U0: np.ndarray, U1: np.ndarray):
+        U0 = _check_state(mesh, U0)
+        ref = np.ascontiguousarray(refined, dtype=np.int32)
+        nfine = len(ref) << mesh.ndim
+        U1 = np.ascontiguousarray(U1, dtype=np.float64)
+        if U1.shape != (nfine,) + mesh.shape()[1:]:
+            raise ValueError(f"fine state shape {U1.shape} != {(nfine,) + mesh.shape()[1:]}")
+        return U0, ref, U1
+
+    def amr_step(self, mesh: Mesh, refined, U0: np.ndarray, U1: np.ndarray, dt_: float):
+        """One two-level step with a given dt (see oracle.c, "two-level AMR"):
+        mesh is the coarse level, refined the coarse block ids split into
+        2^ndim fine blocks each, U0 the coarse state (all coarse blocks), U1
+        the fine state [fine block][var][k][j][i]. Returns (U0new, U1new,
+        nfirst); the parents of U0new are the restriction of U1new."""
+        U0, ref, U1 = self._amr_args(mesh, refined, U0, U1)
+        U0n, U1n = np.empty_like(U0), np.empty_like(U1)
+        m = mesh.c_struct()
+        ip = ref.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        nf = self.L.ora_amr_step(ctypes.byref(m), ip, len(ref), _ptr(U0), _ptr(U1), float(dt_), _ptr(U0n),
+                                 _ptr(U1n))
+        if nf < 0:
+            raise FloatingPointError("non-physical leaf state (rho <= 0 or p <= 0)")
+        return U0n, U1n, int(nf)
+
+    def amr_dt(self, mesh: Mesh, refined, U0: np.ndarray, U1: np.ndarray) -> float:
+        """CFL time step over the leaf cells of both levels."""
+        U0, ref, U1 = self._amr_args(mesh, refined, U0, U1)
+        m = mesh.c_struct()
+        ip = ref.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        return float(self.L.ora_amr_dt(ctypes.byref(m), ip, len(ref), _ptr(U0), _ptr(U1)))
+
+    def amr_run(self, mesh: Mesh, refined, U0: np.ndarray, U1: np.ndarray, nsteps: int):
+        """nsteps two-level steps, each with the dt of its start state.
+        Returns (U0, U1, dts)."""
+        dts = []
+        for _ in range(nsteps):
+            d = self.amr_dt(mesh, refined, U0, U1)
+            if not d > 0:
+                raise FloatingPointError("non-physical state during an AMR run")
+            U0, U1, _ = self.amr_step(mesh, refined, U0, U1, d)
+            dts.append(d)
+        return U0, U1, np.array(dts)
+
+
 _default = Variant()
 set_threads = _default.set_threads
 get_threads = _default.get_threads
@@ -250,3 +304,6 @@ step = _default.step
 stage = _default.stage
 step_rk2 = _default.step_rk2
 run = _default.run
+amr_step = _default.amr_step
+amr_dt = _default.amr_dt
+amr_run = _default.amr_run

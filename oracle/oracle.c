@@ -225,10 +225,33 @@ typedef struct {
     double* R;         /* [...] 1/rho */
     double* FS;        /* [cell][d][side][v] face states (side 0: low face, 1: high face) */
     int* first;        /* [cell] 1 if the cell fell back to first order */
+    const struct ora_amr_src* amr;  /* fine level of a two-level mesh: where cells come from (else NULL) */
+    double* reg;       /* NULL, or this block's face fluxes [2d + side][v][face cell] (flux register) */
+    long out_b;        /* block index of the output (-1: the block's own index) */
 } ora_work;
+
+static double amr_value(const struct ora_amr_src* s, int v, int gi, int gj, int gk);
 
 static long pidx(const ora_work* w, int i, int j, int k) {
     return ((long)(k + w->off[2]) * w->p[1] + (j + w->off[1])) * w->p[0] + (i + w->off[0]);
+}
+
+/* Flux registers: index of the face cell of (i, j, k) on a face normal to
+ * axis d (the two other axes, lower one fastest), and the stride between
+ * faces (the largest face of a block). */
+static long face_cell(const ora_mesh* m, int d, const int loc[3]) {
+    int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
+    return (long)loc[a2] * m->bs[a1] + loc[a1];
+}
+
+static long face_stride(const ora_mesh* m) {
+    long f = 0;
+    for (int d = 0; d < 3; ++d) {
+        int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
+        long n = (long)m->bs[a1] * m->bs[a2];
+        if (n > f) f = n;
+    }
+    return f;
 }
 
 /* Fill the padded conserved array of block (bx, by, bz) from the global state:
@@ -244,7 +267,8 @@ static void fill_padded_block(const ora_mesh* m, const double* U, int bxyz[3], o
                 int gj = bxyz[1] * m->bs[1] + j;
                 int gk = bxyz[2] * m->bs[2] + k;
                 for (int v = 0; v < nv; ++v)
-                    w->U[v * np + pidx(w, i, j, k)] = global_value(m, U, v, gi, gj, gk);
+                    w->U[v * np + pidx(w, i, j, k)] =
+                        w->amr ? amr_value(w->amr, v, gi, gj, gk) : global_value(m, U, v, gi, gj, gk);
             }
 }
 
@@ -387,6 +411,14 @@ static void advance_block(const ora_mesh* m, const double* U, const double* Ubas
                     }
                     /* domain-boundary flux bookkeeping (outflow axes only) */
                     int loc[3] = {i, j, k};
+                    if (w->reg) {    /* flux register: the fluxes through the block's own faces */
+                        long t = face_cell(m, d, loc);
+                        long fsz = face_stride(m);
+                        if (loc[d] == 0)
+                            for (int v = 0; v < nv; ++v) w->reg[((2 * d) * MAXV + v) * fsz + t] = Flo[v];
+                        if (loc[d] == m->bs[d] - 1)
+                            for (int v = 0; v < nv; ++v) w->reg[((2 * d + 1) * MAXV + v) * fsz + t] = Fhi[v];
+                    }
                     if (!m->periodic[d]) {
                         if (bxyz[d] == 0 && loc[d] == 0)
                             for (int v = 0; v < nv; ++v) bflux[v] -= cd[d] * Flo[v];
@@ -396,7 +428,7 @@ static void advance_block(const ora_mesh* m, const double* U, const double* Ubas
                 }
                 long co = ((long)k * m->bs[1] + j) * m->bs[0] + i;
                 for (int v = 0; v < nv; ++v) {
-                    long o = (b * nv + v) * ncell_block(m) + co;
+                    long o = ((w->out_b >= 0 ? w->out_b : b) * nv + v) * ncell_block(m) + co;
                     double us = w->U[v * np + c] - acc[v];
                     Unew[o] = Ubase ? (0.5 * (Ubase[o] + us)) : us;
                 }
@@ -434,6 +466,9 @@ static long sweep(const ora_mesh* m, const double* U, const double* Ubase, int p
         w.R = (double*)malloc(sizeof(double) * np);
         w.FS = (double*)malloc(sizeof(double) * np * 3 * 2 * MAXV);
         w.first = (int*)calloc((size_t)np, sizeof(int));
+        w.amr = NULL;
+        w.reg = NULL;
+        w.out_b = -1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -512,4 +547,273 @@ int ora_run_scheme(const ora_mesh* m, double* U, int nsteps, int rk2, double* dt
 /* nsteps MUSCL-Hancock steps in place (ora_run_scheme with rk2 = 0). */
 int ora_run(const ora_mesh* m, double* U, int nsteps, double* dts, double* bflux_total) {
     return ora_run_scheme(m, U, nsteps, 0, dts, bflux_total);
+}
+
+/* ---------------------------------------------------------------- two-level AMR
+ * Block AMR with flux correction (the paper's section "Experiments": when two
+ * adjacent blocks are at different refinement levels, their boundary fluxes
+ * must be reconciled). The coarse level is the uniform block grid of m; the
+ * blocks listed in `refined` are each covered by 2^ndim fine blocks of the
+ * same cell count and half the cell width (fine block r * 2^ndim + o is child
+ * o of refined[r], octant bits x | y << 1 | z << 2). Both levels advance with
+ * the same dt (no subcycling). Readings:
+ *   - a coarse block under fine blocks (a parent) holds the average of its
+ *     children's cells (restriction) and is not advanced itself;
+ *   - fine guard cells inside a fine block read it; inside an unrefined
+ *     coarse block they take the value of the coarse cell that contains them
+ *     (piecewise-constant prolongation); the fine level applies the boundary
+ *     rule in its own index space;
+ *   - coarse guard cells read the coarse level, parents included;
+ *   - flux correction: a coarse leaf cell next to a refined block is updated
+ *     with the average of the 2^(ndim-1) fine fluxes through its face (summed
+ *     pairwise) instead of its own flux there, so every face carries one flux
+ *     and the total sum_cells U dV is conserved exactly up to rounding;
+ *   - dt = CFL / max over leaf cells of both levels of sum_d (|u_d| + c)/dx_d.
+ * State arrays: coarse [block][var][k][j][i] over all coarse blocks (parents
+ * included), fine [fine block][var][k][j][i]. */
+
+typedef struct ora_amr_src {
+    const ora_mesh* c;     /* coarse level */
+    const int* child0;     /* per coarse block: its first fine block, or -1 (a leaf) */
+    const double* U0;      /* coarse state (parents restricted) */
+    const double* U1;      /* fine state */
+} ora_amr_src;
+
+static long cell_off(const ora_mesh* m, const int loc[3]) {
+    return ((long)loc[2] * m->bs[1] + loc[1]) * m->bs[0] + loc[0];
+}
+
+/* Value of variable v at fine global cell (gi, gj, gk), indices possibly
+ * outside the domain (fine-level boundary rule first). */
+static double amr_value(const ora_amr_src* s, int v, int gi, int gj, int gk) {
+    const ora_mesh* c = s->c;
+    int nv = nvars(c), g[3] = {gi, gj, gk}, f[3], gc[3], bc[3], loc[3];
+    for (int d = 0; d < 3; ++d) {
+        f[d] = (d < c->ndim) ? map_index(g[d], 2 * c->nb[d] * c->bs[d], c->periodic[d]) : 0;
+        gc[d] = f[d] / 2;
+        if (d >= c->ndim) gc[d] = 0;
+        bc[d] = gc[d] / c->bs[d];
+    }
+    long b = bc[0] + (long)c->nb[0] * (bc[1] + (long)c->nb[1] * bc[2]);
+    if (s->child0[b] < 0) {
+        for (int d = 0; d < 3; ++d) loc[d] = gc[d] % c->bs[d];
+        return s->U0[(b * nv + v) * ncell_block(c) + cell_off(c, loc)];
+    }
+    int o = 0;
+    for (int d = 0; d < c->ndim; ++d) {
+        o |= ((f[d] / c->bs[d]) % 2) << d;
+        loc[d] = f[d] % c->bs[d];
+    }
+    for (int d = c->ndim; d < 3; ++d) loc[d] = 0;
+    long fb = s->child0[b] + o;
+    return s->U1[(fb * nv + v) * ncell_block(c) + cell_off(c, loc)];
+}
+
+/* Parents (coarse blocks with children) <- average of their children's cells:
+ * the 2^ndim fine cells (x fastest) summed pairwise, times 1/2^ndim (so equal
+ * values restrict exactly). */
+static void amr_restrict(const ora_mesh* c, const int* child0, const double* U1, double* U0) {
+    int nv = nvars(c), nd = c->ndim;
+    long nc = ncell_block(c), nblk = nblocks(c);
+    double w = (nd == 3) ? 0.125 : 0.25;
+    for (long b = 0; b < nblk; ++b) {
+        if (child0[b] < 0) continue;
+        for (int k = 0; k < c->bs[2]; ++k)
+            for (int j = 0; j < c->bs[1]; ++j)
+                for (int i = 0; i < c->bs[0]; ++i) {
+                    int loc[3] = {i, j, k}, o = 0, fl[3];
+                    for (int d = 0; d < nd; ++d) {
+                        o |= ((2 * loc[d]) / c->bs[d]) << d;
+                        fl[d] = (2 * loc[d]) % c->bs[d];
+                    }
+                    if (nd == 2) fl[2] = 0;
+                    long fb = child0[b] + o;
+                    for (int v = 0; v < nv; ++v) {
+                        double x[8];
+                        int n = 0;
+                        for (int ez = 0; ez < (nd == 3 ? 2 : 1); ++ez)
+                            for (int ey = 0; ey < 2; ++ey)
+                                for (int ex = 0; ex < 2; ++ex) {
+                                    int q[3] = {fl[0] + ex, fl[1] + ey, fl[2] + ez};
+                                    x[n++] = U1[(fb * nv + v) * nc + cell_off(c, q)];
+                                }
+                        double s = (x[0] + x[1]) + (x[2] + x[3]);
+                        if (nd == 3) s = s + ((x[4] + x[5]) + (x[6] + x[7]));
+                        U0[(b * nv + v) * nc + cell_off(c, loc)] = w * s;
+                    }
+                }
+    }
+}
+
+static int* amr_children(const ora_mesh* c, const int* refined, int nref) {
+    long nblk = nblocks(c);
+    int* child0 = (int*)malloc(sizeof(int) * (size_t)nblk);
+    for (long b = 0; b < nblk; ++b) child0[b] = -1;
+    for (int r = 0; r < nref; ++r) child0[refined[r]] = r << c->ndim;
+    return child0;
+}
+
+/* The fine level as a uniform mesh of twice as many blocks per axis (used
+ * for cell widths, block coordinates and its boundary rule). */
+static ora_mesh amr_fine_mesh(const ora_mesh* c) {
+    ora_mesh f = *c;
+    for (int d = 0; d < c->ndim; ++d) f.nb[d] = 2 * c->nb[d];
+    return f;
+}
+
+/* Largest signal speed over the leaf cells of both levels; -1 if a leaf cell
+ * is non-physical. */
+double ora_amr_max_signal_speed(const ora_mesh* c, const int* refined, int nref, const double* U0,
+                                const double* U1) {
+    int nv = nvars(c), nch = 1 << c->ndim;
+    int* child0 = amr_children(c, refined, nref);
+    ora_mesh f = amr_fine_mesh(c);
+    double idxc[3], idxf[3], smax = 0.0;
+    int bad = 0;
+    for (int d = 0; d < 3; ++d) {
+        idxc[d] = 1.0 / cell_width(c, d);
+        idxf[d] = 1.0 / cell_width(&f, d);
+    }
+    long nc = ncell_block(c), nblk = nblocks(c), nfine = (long)nref * nch;
+    for (long b = 0; b < nblk + nfine; ++b) {
+        int fine = b >= nblk;
+        if (!fine && child0[b] >= 0) continue;
+        const double* U = fine ? U1 : U0;
+        long bb = fine ? b - nblk : b;
+        for (long cc = 0; cc < nc; ++cc) {
+            double Uc[MAXV], W[MAXV], r;
+            for (int v = 0; v < nv; ++v) Uc[v] = U[(bb * nv + v) * nc + cc];
+            prim_from_cons(c->ndim, c->gamma, Uc, W, &r);
+            if (!(W[0] > 0.0) || !(W[nv - 1] > 0.0)) bad = 1;
+            double s = cell_signal_speed(c, Uc, fine ? idxf : idxc);
+            if (s > smax) smax = s;
+        }
+    }
+    free(child0);
+    return bad ? -1.0 : smax;
+}
+
+double ora_amr_dt(const ora_mesh* c, const int* refined, int nref, const double* U0, const double* U1) {
+    double s = ora_amr_max_signal_speed(c, refined, nref, U0, U1);
+    if (!(s > 0.0)) return -1.0;
+    return c->cfl / s;
+}
+
+/* One two-level MUSCL-Hancock step with dt: parents restricted from U1, every
+ * leaf block of both levels advanced (fine guards by the rule above), then
+ * the flux correction at coarse-fine faces, then the parents of U0new
+ * restricted from U1new. Returns the first-order cells, or -1 on a
+ * non-physical leaf state. */
+long ora_amr_step(const ora_mesh* c, const int* refined, int nref, const double* U0, const double* U1, double dt,
+                  double* U0new, double* U1new) {
+    int nv = nvars(c), nd = c->ndim, nch = 1 << nd;
+    long nc = ncell_block(c), nblk = nblocks(c), nfine = (long)nref * nch;
+    int* child0 = amr_children(c, refined, nref);
+    ora_mesh f = amr_fine_mesh(c);
+    long fsz = face_stride(c), regsz = 6 * MAXV * fsz;
+    double* P = (double*)malloc(sizeof(double) * (size_t)(nblk * nv * nc));
+    memcpy(P, U0, sizeof(double) * (size_t)(nblk * nv * nc));
+    amr_restrict(c, child0, U1, P);
+    memcpy(U0new, P, sizeof(double) * (size_t)(nblk * nv * nc));
+    double* regc = (double*)calloc((size_t)(nblk * regsz), sizeof(double));
+    double* regf = (double*)calloc((size_t)(nfine > 0 ? nfine * regsz : 1), sizeof(double));
+    ora_amr_src src = {c, child0, P, U1};
+    long nfirst = 0, nbad = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads) reduction(+ : nfirst, nbad)
+#endif
+    {
+        ora_work w;
+        for (int d = 0; d < 3; ++d) {
+            w.off[d] = (d < nd) ? G : 0;
+            w.p[d] = c->bs[d] + 2 * w.off[d];
+        }
+        long np = (long)w.p[0] * w.p[1] * w.p[2];
+        w.U = (double*)malloc(sizeof(double) * np * MAXV);
+        w.W = (double*)malloc(sizeof(double) * np * MAXV);
+        w.R = (double*)malloc(sizeof(double) * np);
+        w.FS = (double*)malloc(sizeof(double) * np * 3 * 2 * MAXV);
+        w.first = (int*)calloc((size_t)np, sizeof(int));
+        double bf[MAXV];
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (long b = 0; b < nblk + nfine; ++b) {
+            for (int v = 0; v < MAXV; ++v) bf[v] = 0.0;
+            if (b < nblk) {                       /* a coarse leaf */
+                if (child0[b] >= 0) continue;
+                w.amr = NULL;
+                w.reg = regc + b * regsz;
+                w.out_b = -1;
+                advance_block(c, P, NULL, 1, dt, b, U0new, bf, &nfirst, &nbad, &w);
+            } else {                              /* a fine block: its coordinates on the fine level */
+                long fb = b - nblk;
+                int pr = refined[fb >> nd], o = (int)(fb & (nch - 1));
+                int pc[3] = {pr % c->nb[0], (pr / c->nb[0]) % c->nb[1], pr / (c->nb[0] * c->nb[1])}, fc[3];
+                for (int d = 0; d < 3; ++d) fc[d] = (d < nd) ? 2 * pc[d] + ((o >> d) & 1) : 0;
+                long ub = fc[0] + (long)f.nb[0] * (fc[1] + (long)f.nb[1] * fc[2]);
+                w.amr = &src;
+                w.reg = regf + fb * regsz;
+                w.out_b = fb;
+                advance_block(&f, U1, NULL, 1, dt, ub, U1new, bf, &nfirst, &nbad, &w);
+            }
+        }
+        free(w.U); free(w.W); free(w.R); free(w.FS); free(w.first);
+    }
+    /* flux correction at the faces between coarse leaves and refined blocks */
+    for (long b = 0; b < nblk; ++b) {
+        if (child0[b] >= 0) continue;
+        int bc[3] = {(int)(b % c->nb[0]), (int)((b / c->nb[0]) % c->nb[1]), (int)(b / ((long)c->nb[0] * c->nb[1]))};
+        for (int d = 0; d < nd; ++d)
+            for (int side = 0; side < 2; ++side) {
+                int nbc[3] = {bc[0], bc[1], bc[2]};
+                nbc[d] += side ? 1 : -1;
+                if (nbc[d] < 0 || nbc[d] >= c->nb[d]) {
+                    if (!c->periodic[d]) continue;
+                    nbc[d] = (nbc[d] + c->nb[d]) % c->nb[d];
+                }
+                long N = nbc[0] + (long)c->nb[0] * (nbc[1] + (long)c->nb[1] * nbc[2]);
+                if (child0[N] < 0) continue;
+                int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;
+                double cdc = dt * (1.0 / cell_width(c, d));
+                for (int t2 = 0; t2 < c->bs[a2]; ++t2)
+                    for (int t1 = 0; t1 < c->bs[a1]; ++t1) {
+                        int loc[3];
+                        loc[d] = side ? c->bs[d] - 1 : 0;
+                        loc[a1] = t1;
+                        loc[a2] = t2;
+                        long t = face_cell(c, d, loc);
+                        /* the children of N on the near side, and their face cells */
+                        int s1 = (2 * t1) / c->bs[a1], s2 = (a2 < nd) ? (2 * t2) / c->bs[a2] : 0;
+                        int o = ((side ? 0 : 1) << d) | (s1 << a1) | (s2 << a2);
+                        long fb = child0[N] + o;
+                        const double* rf = regf + fb * regsz + ((2 * d + (side ? 0 : 1)) * MAXV) * fsz;
+                        const double* rc = regc + b * regsz + ((2 * d + side) * MAXV) * fsz;
+                        for (int v = 0; v < nv; ++v) {
+                            double avg;
+                            int fl[3];
+                            fl[d] = 0;
+                            fl[a1] = 2 * t1 - s1 * c->bs[a1];
+                            fl[a2] = (a2 < nd) ? 2 * t2 - s2 * c->bs[a2] : 0;
+                            if (nd == 3) {
+                                int q00[3] = {fl[0], fl[1], fl[2]}, q10[3], q01[3], q11[3];
+                                for (int e = 0; e < 3; ++e) { q10[e] = q00[e]; q01[e] = q00[e]; q11[e] = q00[e]; }
+                                q10[a1] += 1; q01[a2] += 1; q11[a1] += 1; q11[a2] += 1;
+                                avg = 0.25 * ((rf[v * fsz + face_cell(c, d, q00)] + rf[v * fsz + face_cell(c, d, q10)]) +
+                                              (rf[v * fsz + face_cell(c, d, q01)] + rf[v * fsz + face_cell(c, d, q11)]));
+                            } else {
+                                int q0[3] = {fl[0], fl[1], 0}, q1[3] = {fl[0], fl[1], 0};
+                                q1[a1] += 1;
+                                avg = 0.5 * (rf[v * fsz + face_cell(c, d, q0)] + rf[v * fsz + face_cell(c, d, q1)]);
+                            }
+                            double corr = cdc * (rc[v * fsz + t] - avg);
+                            long oi = (b * nv + v) * nc + cell_off(c, loc);
+                            U0new[oi] = side ? (U0new[oi] + corr) : (U0new[oi] - corr);
+                        }
+                    }
+            }
+    }
+    amr_restrict(c, child0, U1new, U0new);
+    free(P); free(regc); free(regf); free(child0);
+    return nbad ? -1 : nfirst;
 }

@@ -415,3 +415,53 @@ def ramp_state(spec: MeshSpec, var: str, delta: float = 0.1, u: float = 10.0, ba
     rho, p = (flat, ramp) if var == "p" else (ramp, flat)
     vel = [np.full(x.shape, u)] + [np.zeros(x.shape)] * (spec.ndim - 1)
     return to_blocks(spec, _globalize(spec, cons_from_prim_global(spec, rho, vel, p)))
+
+
+# ------------------------------------------------------------------ two-level meshes
+
+def fine_spec(spec: MeshSpec) -> MeshSpec:
+    """The fine level of a two-level mesh as a uniform mesh: twice the blocks
+    per active axis, the same block size, half the cell width."""
+    nb = tuple(2 * spec.nb[d] if d < spec.ndim else spec.nb[d] for d in range(3))
+    return replace(spec, nb=nb)
+
+
+def refined_blocks(spec: MeshSpec, kind: str = "sphere", frac: float = 0.3) -> np.ndarray:
+    """Coarse block ids to refine: blocks whose centres lie within radius frac
+    of the domain centre ("sphere"), or in the upper half along x ("half")."""
+    ids = []
+    for b in range(spec.nblocks):
+        bc = (b % spec.nb[0], (b // spec.nb[0]) % spec.nb[1], b // (spec.nb[0] * spec.nb[1]))
+        c = [(bc[d] + 0.5) / spec.nb[d] if d < spec.ndim else 0.5 for d in range(3)]
+        if kind == "sphere":
+            inside = sum((c[d] - 0.5) ** 2 for d in range(spec.ndim)) <= frac ** 2
+        else:
+            inside = c[0] > 0.5
+        if inside:
+            ids.append(b)
+    return np.array(ids, dtype=np.int32)
+
+
+def amr_split(spec: MeshSpec, refined, Ub_fine: np.ndarray):
+    """Initial data of a two-level mesh from a state on the uniform fine mesh
+    (block array of fine_spec(spec)): the coarse state is the mean of each
+    2^ndim group of fine cells, the fine state holds the children of the
+    refined blocks [refined index * 2^ndim + octant][var][k][j][i] (octant bits
+    x | y << 1 | z << 2)."""
+    fs = fine_spec(spec)
+    G = from_blocks(fs, Ub_fine)                  # var, z, y, x
+    nv = spec.nvar
+    if spec.ndim == 3:
+        Gc = G.reshape(nv, G.shape[1] // 2, 2, G.shape[2] // 2, 2, G.shape[3] // 2, 2).mean(axis=(2, 4, 6))
+    else:
+        Gc = G.reshape(nv, 1, G.shape[2] // 2, 2, G.shape[3] // 2, 2).mean(axis=(3, 5))
+    U0 = to_blocks(spec, Gc)
+    nch = 1 << spec.ndim
+    U1 = np.empty((len(refined) * nch,) + spec.block_shape()[1:])
+    for r, b in enumerate(refined):
+        bc = (b % spec.nb[0], (b // spec.nb[0]) % spec.nb[1], b // (spec.nb[0] * spec.nb[1]))
+        for o in range(nch):
+            fc = [2 * bc[d] + ((o >> d) & 1) if d < spec.ndim else 0 for d in range(3)]
+            fb = fc[0] + fs.nb[0] * (fc[1] + fs.nb[1] * fc[2])
+            U1[r * nch + o] = Ub_fine[fb]
+    return U0, U1

@@ -2,7 +2,7 @@
 
 Each case copies oracle/oracle.c, replaces one expression with a plausible
 mistake (a dropped term, a wrong sign, a wrong index, a wrong constant, a
-wrong boundary rule, a wrong first-order fallback rule), compiles the copy
+wrong boundary rule, a wrong first-order fallback or refinement rule), compiles the copy
 with the oracle's own flags, binds the oracle API to it, and runs the pin
 tests of tests/test_oracle_pins.py against it: at least one pin must fail. Mistakes are planted only in a temporary copy
 of the oracle, on the CPU.
@@ -17,6 +17,7 @@ import oracle
 from oracle import build as obuild
 
 from . import test_oracle_pins as pins
+from . import test_oracle_amr_pins as amr
 from . import test_oracle_rk2_pins as rk2
 
 MUTATIONS = {
@@ -55,6 +56,17 @@ MUTATIONS = {
                 if (0) {"""),
     "fallback_to_half_step_state": ("for (int v = 0; v < nv; ++v) fs[(d * 2 + s) * MAXV + v] = Wc[v];",
                                     "for (int v = 0; v < nv; ++v) fs[(d * 2 + s) * MAXV + v] = Wbar[v];"),
+    # the two-level AMR step
+    "amr_no_flux_correction": ("U0new[oi] = side ? (U0new[oi] + corr) : (U0new[oi] - corr);",
+                               "U0new[oi] = U0new[oi] + 0.0 * corr;"),
+    "amr_flux_correction_sign": ("U0new[oi] = side ? (U0new[oi] + corr) : (U0new[oi] - corr);",
+                                 "U0new[oi] = side ? (U0new[oi] - corr) : (U0new[oi] + corr);"),
+    "amr_reflux_far_children": ("int o = ((side ? 0 : 1) << d) | (s1 << a1) | (s2 << a2);",
+                                "int o = ((side ? 1 : 0) << d) | (s1 << a1) | (s2 << a2);"),
+    "amr_restrict_weight": ("double w = (nd == 3) ? 0.125 : 0.25;", "double w = (nd == 3) ? 0.25 : 0.5;"),
+    "amr_octant_order": ("o |= ((f[d] / c->bs[d]) % 2) << d;", "o |= ((f[d] / c->bs[d]) % 2) << (c->ndim - 1 - d);"),
+    "amr_fine_cell_width": ("for (int d = 0; d < c->ndim; ++d) f.nb[d] = 2 * c->nb[d];",
+                            "for (int d = 0; d < c->ndim; ++d) f.nb[d] = c->nb[d];"),
     # the Heun RK2 integrator
     "rk2_forward_euler_twice": ("Unew[o] = Ubase ? (0.5 * (Ubase[o] + us)) : us;", "Unew[o] = us;"),
     "rk2_stage_weights": ("(0.5 * (Ubase[o] + us))", "((0.25 * Ubase[o]) + (0.75 * us))"),
@@ -90,6 +102,10 @@ PIN_TESTS = [
     ("rk2_sod_exact", lambda o: rk2.test_rk2_sod_matches_exact_solution_and_rows_are_identical(o)),
     ("rk2_order_advection", lambda o: rk2.test_rk2_second_order_on_advected_density_wave(o)),
     ("rk2_order_acoustic", lambda o: rk2.test_rk2_second_order_on_smooth_acoustic_wave(o)),
+    ("amr_free_stream", lambda o: amr.test_free_stream_is_preserved_across_levels(o, 3)),
+    ("amr_all_refined", lambda o: amr.test_everything_refined_is_the_uniform_fine_step(o, 3)),
+    ("amr_conservation", lambda o: amr.test_leaf_totals_are_conserved_on_a_periodic_box(o, 3)),
+    ("amr_conservation_2d", lambda o: amr.test_leaf_totals_are_conserved_on_a_periodic_box(o, 2)),
 ]
 
 
