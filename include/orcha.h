@@ -398,6 +398,60 @@ ORCHA_API orcha_status orcha_server_get_stats(orcha_server* server, orcha_server
 ORCHA_API orcha_status orcha_autotune(int32_t ndim, const int32_t bs[3], orcha_task hydro_task, int32_t nblocks,
                                       const char* cache_path, int32_t* tx, int32_t* ty, double* ms_out);
 
+/* ------------------------------------------------------------------ two-level AMR
+ * Block AMR with flux correction. The paper's application runs on an AMR
+ * mesh, where adjacent blocks at different refinement levels need their
+ * boundary fluxes reconciled (flux correction); the paper does that in a
+ * second, low-intensity step outside its task functions (section
+ * "Experiments", Spark paragraph). Here the whole two-level step runs on the
+ * device.
+ *
+ * The coarse level is the uniform block grid of a mesh descriptor (its two
+ * state buffers and dt_dev). Each of the nref coarse blocks in `refined` is
+ * covered by 2^ndim fine blocks of the same cell count and half the cell
+ * width; fine block f is child f % 2^ndim (octant bits x | y << 1 | z << 2)
+ * of refined[f >> ndim], stored in two caller-owned fine buffers of
+ * orcha_amr_fine_elems() doubles each ([fine block][var][k][j][i] over the
+ * padded block, 16-byte aligned). A refined coarse block (a parent) holds the
+ * average of its children and is not advanced. One step, both levels with
+ * the same dt (FP64 MUSCL-Hancock):
+ *   parents <- restriction of their children (pairwise sums, times 2^-ndim);
+ *   guard fill: coarse from the coarse level (parents included); fine from
+ *     the fine blocks, or the coarse cell that contains the guard cell
+ *     (piecewise-constant prolongation); the boundary rule applies on each
+ *     level's own index space;
+ *   every coarse leaf and every fine block advances, recording the fluxes
+ *     through its faces;
+ *   flux correction: a coarse leaf cell next to a refined block is corrected
+ *     by (dt/dx)(F_coarse - average of the 2^(ndim-1) fine fluxes) through
+ *     that face, so the total of U dV over the leaf cells is conserved;
+ *   parents <- restriction; dt = cfl / max over leaf cells of both levels of
+ *     sum_d (|u_d| + c) / dx_d.
+ * Calls are stream-ordered like the mesh calls; create allocates the flux
+ * registers (6 faces x nvar x the largest face of a block, per block) and
+ * small index arrays. */
+typedef struct orcha_amr orcha_amr;
+
+/* Doubles in one fine state buffer (0 if the descriptor is invalid). */
+ORCHA_API size_t orcha_amr_fine_elems(const orcha_mesh_desc* coarse, int32_t nref);
+/* Errors: INVALID (descriptor, ids out of range or repeated, buffers), OOM, CUDA. */
+ORCHA_API orcha_status orcha_amr_create(const orcha_mesh_desc* coarse, const int32_t* refined, int32_t nref,
+                                        double* fine_state0_dev, double* fine_state1_dev, orcha_amr** out);
+ORCHA_API orcha_status orcha_amr_destroy(orcha_amr* amr);
+/* Copy interiors into / out of the current buffers of both levels: coarse
+ * [block][var][k][j][i] over all coarse blocks (a parent's cells are
+ * replaced by its children's average at the next advance), fine [fine
+ * block][var][k][j][i]. host_ptr != 0: host memory (staged; the call waits
+ * for the copy), else device memory. */
+ORCHA_API orcha_status orcha_amr_load(orcha_amr* amr, const double* coarse, const double* fine, int32_t host_ptr,
+                                      void* stream);
+ORCHA_API orcha_status orcha_amr_store(orcha_amr* amr, double* coarse, double* fine, int32_t host_ptr, void* stream);
+/* nsteps two-level steps; init_dt != 0 first forms dt from the current leaf
+ * cells, otherwise dt_dev must hold it; each step leaves the next dt there. */
+ORCHA_API orcha_status orcha_amr_advance(orcha_amr* amr, int32_t nsteps, int32_t init_dt, void* stream);
+/* As orcha_mesh_poll, for both levels. */
+ORCHA_API orcha_status orcha_amr_poll(orcha_amr* amr, void* stream, int32_t* device_error);
+
 /* ------------------------------------------------------------------ no-allocation CFL step
  * The paper has no counterpart to this call. It serves callers that cannot
  * let a library allocate device memory (for example a host code whose own

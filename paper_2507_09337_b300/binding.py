@@ -153,6 +153,14 @@ SIGNATURES = {
     "orcha_selftest_fp64_emulation": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_dword": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "orcha_measure_fp64_rate": (_st, [_i32, ctypes.POINTER(ctypes.c_double)]),
+    "orcha_amr_fine_elems": (ctypes.c_size_t, [ctypes.POINTER(orcha_mesh_desc), _i32]),
+    "orcha_amr_create": (_st, [ctypes.POINTER(orcha_mesh_desc), ctypes.POINTER(_i32), _i32, _vp, _vp,
+                               ctypes.POINTER(_vp)]),
+    "orcha_amr_destroy": (_st, [_vp]),
+    "orcha_amr_load": (_st, [_vp, _vp, _vp, _i32, _vp]),
+    "orcha_amr_store": (_st, [_vp, _vp, _vp, _i32, _vp]),
+    "orcha_amr_advance": (_st, [_vp, _i32, _i32, _vp]),
+    "orcha_amr_poll": (_st, [_vp, _vp, ctypes.POINTER(_i32)]),
     "orcha_last_error": (ctypes.c_char_p, []),
 }
 
@@ -367,6 +375,40 @@ def orcha_measure_fp64_rate(op: int = 0) -> float:
     return r.value
 
 
+def orcha_amr_fine_elems(desc: orcha_mesh_desc, nref: int) -> int:
+    return int(lib().orcha_amr_fine_elems(ctypes.byref(desc), int(nref)))
+
+
+def orcha_amr_create(desc: orcha_mesh_desc, refined, fine0_ptr: int, fine1_ptr: int) -> int:
+    ids = np.ascontiguousarray(refined, dtype=np.int32)
+    h = _vp()
+    _check(lib().orcha_amr_create(ctypes.byref(desc), ids.ctypes.data_as(ctypes.POINTER(_i32)), len(ids),
+                                  fine0_ptr, fine1_ptr, ctypes.byref(h)))
+    return h.value
+
+
+def orcha_amr_destroy(amr: int) -> None:
+    _check(lib().orcha_amr_destroy(amr))
+
+
+def orcha_amr_load(amr: int, coarse_ptr: int, fine_ptr: int | None, host_ptr: bool, stream=None) -> None:
+    _check(lib().orcha_amr_load(amr, coarse_ptr, fine_ptr, int(bool(host_ptr)), _stream_ptr(stream)))
+
+
+def orcha_amr_store(amr: int, coarse_ptr: int, fine_ptr: int | None, host_ptr: bool, stream=None) -> None:
+    _check(lib().orcha_amr_store(amr, coarse_ptr, fine_ptr, int(bool(host_ptr)), _stream_ptr(stream)))
+
+
+def orcha_amr_advance(amr: int, nsteps: int, init_dt: bool, stream=None) -> None:
+    _check(lib().orcha_amr_advance(amr, int(nsteps), int(bool(init_dt)), _stream_ptr(stream)))
+
+
+def orcha_amr_poll(amr: int, stream=None) -> int:
+    err = _i32()
+    _check(lib().orcha_amr_poll(amr, _stream_ptr(stream), ctypes.byref(err)))
+    return err.value
+
+
 def orcha_last_error() -> str:
     return lib().orcha_last_error().decode()
 
@@ -462,3 +504,60 @@ class Mesh:
 
     def dt_value(self) -> float:
         return float(self.dt.item())
+
+
+class AmrMesh:
+    """A two-level mesh (orcha_amr_*) whose coarse and fine state buffers and
+    dt are torch tensors on one CUDA device."""
+
+    def __init__(self, spec: wl.MeshSpec, refined, device: str = "cuda:0"):
+        import torch
+        self.spec = spec
+        self.refined = np.ascontiguousarray(refined, dtype=np.int32)
+        self.coarse = Mesh(spec, device=device)
+        self.device = self.coarse.device
+        n1 = orcha_amr_fine_elems(self.coarse.desc, len(self.refined))
+        with torch.cuda.device(self.device):
+            self.fine = [torch.zeros(max(n1, 2), dtype=torch.float64, device=self.device) for _ in range(2)]
+        # the AMR object makes its own coarse-level mesh over the same buffers
+        self.handle = orcha_amr_create(self.coarse.desc, self.refined, self.fine[0].data_ptr(),
+                                       self.fine[1].data_ptr())
+
+    @property
+    def nfine(self) -> int:
+        return len(self.refined) << self.spec.ndim
+
+    def close(self):
+        if getattr(self, "handle", None):
+            orcha_amr_destroy(self.handle)
+            self.handle = None
+        if getattr(self, "coarse", None) is not None:
+            self.coarse.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, U0: np.ndarray, U1: np.ndarray):
+        import torch
+        a = torch.from_numpy(np.ascontiguousarray(U0, dtype=np.float64)).pin_memory()
+        b = torch.from_numpy(np.ascontiguousarray(U1, dtype=np.float64)).pin_memory()
+        orcha_amr_load(self.handle, a.data_ptr(), b.data_ptr() if self.nfine else None, True)
+
+    def store(self):
+        import torch
+        a = torch.empty(self.spec.block_shape(), dtype=torch.float64).pin_memory()
+        b = torch.empty((self.nfine,) + self.spec.block_shape()[1:], dtype=torch.float64).pin_memory()
+        orcha_amr_store(self.handle, a.data_ptr(), b.data_ptr() if self.nfine else None, True)
+        return a.numpy().copy(), b.numpy().copy()
+
+    def advance(self, nsteps: int, init_dt: bool = True, stream=None):
+        orcha_amr_advance(self.handle, nsteps, init_dt, stream)
+
+    def poll(self, stream=None) -> int:
+        return orcha_amr_poll(self.handle, stream)
+
+    def dt_value(self) -> float:
+        return float(self.coarse.dt.item())

@@ -308,22 +308,37 @@ struct GlobalIO {
     static constexpr bool kOut = false;     // new values into the scratch
     static constexpr int kRaise = 1;        // 0: none; 1: m.smax (RK: stage 2); 2: the inner cells into io.smax2
     static constexpr int kThreads = 0;      // 0: the variant's own thread count
+    static constexpr bool kReg = false;     // record the fluxes through the block's faces (FluxRegIO)
     double* scratch = nullptr;
     unsigned long long* smax2 = nullptr;    // kRaise 2: per-block maxima of the intermediate state
+    double* reg = nullptr;
+    int fsz = 0;
 };
 template <int NTH, int RAISE>
 struct ScratchOutIO {
-    static constexpr bool kIn = false, kOut = true;
+    static constexpr bool kIn = false, kOut = true, kReg = false;
     static constexpr int kRaise = RAISE, kThreads = NTH;
     double* scratch;
     unsigned long long* smax2;
+    double* reg;
+    int fsz;
 };
 template <int NTH>
 struct ScratchInIO {
-    static constexpr bool kIn = true, kOut = false;
+    static constexpr bool kIn = true, kOut = false, kReg = false;
     static constexpr int kRaise = 1, kThreads = NTH;
     double* scratch;
     unsigned long long* smax2;
+    double* reg;
+    int fsz;
+};
+// The one-step task that also records, per block, the flux through every
+// cell of its six faces (the flux registers of a two-level mesh's flux
+// correction): reg[((blk * 6 + 2 d + side) * nvar + v) * fsz + face cell],
+// face cell = the two other axes' indices, lower axis fastest; packet path
+// (whole blocks) only.
+struct FluxRegIO : GlobalIO {
+    static constexpr bool kReg = true;
 };
 
 // One column tile of one block: the z sweep over interior planes [z0, z1)
@@ -908,6 +923,14 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                 T F[NV];
                 hll<T, NDIM, true>(L, R, F, g, igm1);
                 Fz[0] = F[0]; Fz[3] = F[1]; Fz[1] = F[2]; Fz[2] = F[3]; Fz[4] = F[4];
+                if constexpr (IO::kReg) {      // the block's low (p = 0) and high (p = bz) z faces
+                    if (p == 0 || p == bz) {
+                        double* r = io.reg + ((long long)blk * 6 + (p == 0 ? 4 : 5)) * NV * io.fsz +
+                                    ((y0 + tj) * m.bs[0] + (x0 + ti));
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) r[(long long)v * io.fsz] = P<T>::to_double(Fz[v]);
+                    }
+                }
             }
             if (p >= z0 + 1) {
                 // plane q of the column: block qb above blk, in-block plane ql
@@ -947,6 +970,21 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             if (owner) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) { zp_prev[v] = zhi[v]; Fz_prev[v] = Fz[v]; }
+            }
+        }
+        if constexpr (IO::kReg) {             // the block's x and y faces in plane p
+            if (inner && owner) {
+                const int i = x0 + ti, j = y0 + tj, k = (NDIM == 3) ? p : 0;
+                const long long rb = (long long)blk * 6 * NV * io.fsz;
+                auto put = [&](int face, const S* src, int t) {
+                    double* r = io.reg + rb + (long long)face * NV * io.fsz + t;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) r[(long long)v * io.fsz] = P<T>::to_double(P<T>::ld(&src[v * R1N]));
+                };
+                if (i == 0) put(0, sGx + o1 - 1, k * m.bs[1] + j);
+                if (i == m.bs[0] - 1) put(1, sGx + o1, k * m.bs[1] + j);
+                if (j == 0) put(2, sGy + o1 - R1X, k * m.bs[0] + i);
+                if (j == m.bs[1] - 1) put(3, sGy + o1, k * m.bs[0] + i);
             }
         }
         if (inner && owner) {
@@ -996,17 +1034,17 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
 // Packet path: one CTA per (packet block, column tile); guards come from the
 // padded block.
-template <int NDIM, int TX, int TY, class T, bool RK = false, bool FX = false>
+template <int NDIM, int TX, int TY, class T, bool RK = false, bool FX = false, class IO = GlobalIO>
 __global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<T, RK>())
 hydro_kernel(const MeshDev m, const int* __restrict__ blk_ids, int tiles_x, int tiles_y,
-             const double* __restrict__ Uin, double* __restrict__ Uout, int stage) {
+             const double* __restrict__ Uin, double* __restrict__ Uout, int stage, IO io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[32];
     const int ntile = tiles_x * tiles_y;
     const int blk = blk_ids[blockIdx.x / ntile];
     const int tile = blockIdx.x % ntile;
-    hydro_tile<NDIM, TX, TY, T, false, RK, FX>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY, Uin, Uout,
-                                           smem_raw, red, 0, -1, stage);
+    hydro_tile<NDIM, TX, TY, T, false, RK, FX, IO>(m, blk, (tile % tiles_x) * TX, (tile / tiles_x) * TY, Uin, Uout,
+                                               smem_raw, red, 0, -1, stage, io);
 }
 
 }  // namespace orcha

@@ -430,7 +430,8 @@ static cudaError_t launch_hydro_t(const MeshDev& m, const int* ids, int n, const
     const size_t smem = Tl::template smem_bytes<typename P<T>::store>();
     auto kern = hydro_kernel<NDIM, TX, TY, T, RK, FX>;
     const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
-    kern<<<dim3((unsigned)(n * tx * ty)), dim3(Tl::template nb<T, RK>()), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage);
+    kern<<<dim3((unsigned)(n * tx * ty)), dim3(Tl::template nb<T, RK>()), smem, st>>>(m, ids, tx, ty, Uin, Uout, stage,
+                                                                                    GlobalIO{});
     return cudaGetLastError();
 }
 

@@ -77,6 +77,21 @@ def main():
         res_rk[f"batch_{tile[0]}x{tile[1]}_bitwise"] = bool(np.array_equal(G, OR)) and err == 0
     print(json.dumps(res_tb), flush=True)
     print(json.dumps(res_rk), flush=True)
+    # the two-level AMR step
+    amr = wl.MeshSpec(ndim=3, nb=(3, 3, 3), bs=(8, 8, 8), periodic=(1, 0, 1))
+    refined = wl.refined_blocks(amr, "sphere", 0.35)
+    A0, A1 = wl.amr_split(amr, refined, wl.random_blocky_state(wl.fine_spec(amr), 13))
+    O0, O1, _ = oracle.amr_run(oracle.Mesh(**amr.oracle_kwargs()), refined, A0, A1, 4)
+    a = B.AmrMesh(amr, refined)
+    try:
+        a.load(A0, A1)
+        a.advance(4, init_dt=True)
+        err = a.poll()
+        G0, G1 = a.store()
+    finally:
+        a.close()
+    print(json.dumps({"case": "amr", "coarse_bitwise": bool(np.array_equal(G0, O0)) and err == 0,
+                      "fine_bitwise": bool(np.array_equal(G1, O1))}), flush=True)
 
 
 if __name__ == "__main__":

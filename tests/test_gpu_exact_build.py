@@ -5,7 +5,8 @@ sequence too), 3D Sedov 128^3 in packets of 64 (10 steps), random jumps with
 every tile shape (4 steps), through the packet path and the persistent batch,
 Heun RK2 steps on 2D Sod, and one step with many first-order fallback cells
 (smeared random jumps at 40x the CFL time step; the ramp hand cases), and the
-fused launches (two Hancock steps at one dt; a whole Heun step). The library variant is loaded in a child
+fused launches (two Hancock steps at one dt; a whole Heun step), and four
+two-level AMR steps. The library variant is loaded in a child
 process (a process holds one liborcha)."""
 import json
 import os
@@ -39,7 +40,7 @@ def results():
 
 
 @pytest.mark.parametrize("case", ["sod64", "sedov128", "jumps", "sod64_rk2", "fallback40", "fallback_ramp_p",
-                                  "fallback_ramp_rho", "tb2", "rk2_fused"])
+                                  "fallback_ramp_rho", "tb2", "rk2_fused", "amr"])
 def test_exact_build_is_bitwise_the_oracle(results, case):
     d = results[case]
     flags = {k: v for k, v in d.items() if k.endswith("_bitwise")}
