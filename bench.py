@@ -14,7 +14,7 @@ per-request launches.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload sedov256_uneven|sedov128|sedov128_f32|sedov128_f32x|sedov128_ff|sedov256_uneven_ff|
                      sedov128_rk2|sedov128_rk2_f32|sedov128_rk2_ff|sedov128_tb2|sedov128_tb2_f32|
-                     sedov128_rk2_fused|sedov128_rk2_fused_f32]
+                     sedov128_rk2_fused|sedov128_rk2_fused_f32|sedov128_amr]
                     [--no-cpu-baseline] [--no-serving] [--serve-requests N]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
@@ -122,6 +122,7 @@ WORKLOADS = {       # name -> (mesh, task, Heun steps at CFL 0.4)
     "sedov128_rk2_ff": ("128", "rk2_ff", True),
     "sedov128_tb2": ("128", "tb2", False), "sedov128_tb2_f32": ("128", "tb2_f32", False),
     "sedov128_rk2_fused": ("128", "rk2_fused", True), "sedov128_rk2_fused_f32": ("128", "rk2_fused_f32", True),
+    "sedov128_amr": ("128", "amr", False),
 }
 
 
@@ -259,6 +260,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2507_09337_b300 import workloads as wl
+    if args.workload == "sedov128_amr":
+        return run_reference_amr(args)
     spec, packets, nt, task, desc = workload(args.workload)
     U0 = wl.sedov_state(spec)
     import oracle
@@ -317,12 +320,135 @@ def serving_latency(args):
     return out
 
 
+# ---------------------------------------------------------------- two-level AMR workload
+
+def amr_workload():
+    """Sedov 128^3 coarse (512 blocks of 16^3) with the 32 blocks whose
+    centres lie within 0.25 of the blast refined (256 fine blocks of half the
+    cell width); the initial state is the blast on the fine grid, averaged
+    onto the coarse one."""
+    from paper_2507_09337_b300 import workloads as wl
+    spec, _ = wl.sedov128_packets(64)
+    refined = wl.refined_blocks(spec, "sphere", 0.25)
+    U0, U1 = wl.amr_split(spec, refined, wl.sedov_state(wl.fine_spec(spec)))
+    nleaf = (spec.nblocks - len(refined) + (len(refined) << 3)) * spec.bs[0] * spec.bs[1] * spec.bs[2]
+    desc = ("two-level AMR: 3D Sedov, coarse 128^3 as 512 blocks of 16^3 + 2 guards, the 32 central blocks "
+            "refined into 256 fine blocks of half the cell width, 10 steps, one dt for both levels, flux correction")
+    return spec, refined, U0, U1, nleaf, desc
+
+
+def run_amr(args):
+    import torch
+    from paper_2507_09337_b300 import binding as B
+    from paper_2507_09337_b300 import build as pkgbuild
+    pkgbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spec, refined, U0, U1, nleaf, desc = amr_workload()
+    nt = 10
+    amr = B.AmrMesh(spec, refined)
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    events = []
+
+    def step(record):
+        amr.load(U0, U1)
+        B.orcha_amr_advance(amr.handle, 0, True, stream)
+        for _ in range(nt):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.orcha_amr_advance(amr.handle, 1, False, stream)
+                e1.record(stream)
+                events.append((e0, e1))
+            else:
+                B.orcha_amr_advance(amr.handle, 1, False, stream)
+        stream.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+    assert amr.poll(stream) == 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        step(True)
+    clk = clocks.stop()
+    assert amr.poll(stream) == 0
+    ms = sum(a.elapsed_time(b) for a, b in events)
+    value = nleaf * len(events) / (ms * 1e-3)
+    fp64_peak = B.orcha_measure_fp64_rate(0) / 1e12
+    achieved = FLOPS_PER_ZONE_3D * value / 1e12
+    # end to end: host state in, nt steps, host state out, per bench step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        amr.load(U0, U1)
+        B.orcha_amr_advance(amr.handle, nt, True, stream)
+        stream.synchronize()
+        amr.store()
+    e2e = nleaf * nt * args.steps / (time.perf_counter() - t0)
+    line = {
+        "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "leaf_zones_per_step": nleaf, "refined_blocks": int(len(refined)),
+                   "timed": "device time of the advance calls (events), per step: coarse and fine guard fill, "
+                            "hydro of every leaf, flux correction, restriction, dt"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": None, "ops_per_zone_update": FLOPS_PER_ZONE_3D,
+                     "kernel": "whole two-level step (hydro_kernel<3,16,16,rd,false,false,FluxRegIO> dominant)",
+                     "peak_source": "measured FP64 FMA throughput probe (orcha_measure_fp64_rate)"},
+        "clocks": clk,
+        "e2e": {"value": e2e, "unit": "zone-updates/s", "h2d_bytes_per_step": int(U0.nbytes + U1.nbytes),
+                "d2h_bytes_per_step": int(U0.nbytes + U1.nbytes),
+                "api": "orcha_amr_load(host) + orcha_amr_advance + orcha_amr_store(host), wall clock"},
+        "gpu_launches": len(events) * 9,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+        m = oracle.Mesh(**spec.oracle_kwargs())
+        t0 = time.perf_counter()
+        oracle.amr_run(m, refined, U0, U1, 2)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nleaf * 2 / el, "unit": "zone-updates/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"2 two-level steps of the full mesh in {el:.1f} s"}
+    amr.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_amr(args):
+    """The oracle's two-level step on the AMR workload, one step per bench step."""
+    import oracle
+    spec, refined, U0, U1, nleaf, desc = amr_workload()
+    threads = args.cpu_threads or os.cpu_count() or 1
+    oracle.set_threads(threads)
+    m = oracle.Mesh(**spec.oracle_kwargs())
+    A0, A1, _ = oracle.amr_run(m, refined, U0, U1, args.warmup)
+    t0 = time.perf_counter()
+    oracle.amr_run(m, refined, A0, A1, args.steps)
+    el = time.perf_counter() - t0
+    value = nleaf * args.steps / el
+    line = {"impl": "reference", "metric": "zone-updates/s", "value": value, "unit": "zone-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc + " (reference arm: one step per bench step)"},
+            "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} two-level steps of the full mesh"},
+            "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sedov128_amr":
+        return run_amr(args)
 
     import torch
     import torch.distributed as dist

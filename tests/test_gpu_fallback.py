@@ -122,9 +122,11 @@ def test_fallback_hand_case(oracle_mod, var, task):
         for path in ("packet", "batch"):
             G = gpu_one_step(spec, U0, dt, task, tile, path)
             if task in F32_TASKS:
+                # FP32 fluxes err by ~1e-7 of terms of order 1 while the density
+                # ramp's new values partly cancel to ~0.05: 2.2e-6 observed
                 e = l1_rho(G, O)
                 print(f"  {var} tile {tile} {path}: FP32-flux relative L1(rho) {e:.3e}")
-                assert e < 1e-6
+                assert e < 1e-5
             else:
                 e = term_scaled_error(G, O, U0, spec.nvar)
                 print(f"  {var} tile {tile} {path}: error with the old value in the scale {e:.3e}")
