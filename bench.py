@@ -53,7 +53,8 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 20
 
 KERNEL_SOURCES = ["paper_2507_09337_b300/csrc/common.cuh", "paper_2507_09337_b300/csrc/hydro.cuh",
                   "paper_2507_09337_b300/csrc/persistent.cuh", "paper_2507_09337_b300/csrc/dword.cuh",
-                  "paper_2507_09337_b300/csrc/softfp64.cuh"]
+                  "paper_2507_09337_b300/csrc/softfp64.cuh", "paper_2507_09337_b300/csrc/fused.cuh",
+                  "paper_2507_09337_b300/csrc/amr.cu"]
 
 
 def kernel_source_hash() -> str:

@@ -2,7 +2,7 @@
 server (orcha_server_*) or through plain per-request packet launches.
 
     python -m paper_2507_09337_b300.serve [--rates 1000,2000,...] [--requests N]
-           [--task f32flux|fp64|ff] [--budget-gb 64] [--max-blocks 512] [--out FILE]
+           [--task f32flux|f32flux_ffsum|fp64|ff] [--budget-gb 64] [--max-blocks 512] [--out FILE]
 
 Each request is an independent 3D problem (K ~ U[1, max_blocks] blocks of
 8^3, 16^3 or 32^3 cells, Sedov-like or Sod-like two-region initial state
@@ -142,7 +142,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--requests", type=int, default=10000)
-    ap.add_argument("--task", choices=["f32flux", "fp64", "ff"], default="f32flux")
+    ap.add_argument("--task", choices=["f32flux", "f32flux_ffsum", "fp64", "ff"], default="f32flux")
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--max-blocks", type=int, default=512)
     ap.add_argument("--nsteps", type=int, default=1)

@@ -13,9 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # summary -> kernel variants bench.py may time on that workload
 CAPTURED = {
     "persistent_kernel_fp64_sedov128.md": ["persistent_kernel<3,16,16,rd>"],
-    "persistent_kernel_f32flux_sedov128.md": ["persistent_kernel<3,16,8,float>", "persistent_kernel<3,16,16,float>"],
+    "persistent_kernel_fp64_sedov256.md": ["persistent_kernel<3,16,16,rd>"],
+    "persistent_kernel_f32flux_sedov128.md": ["persistent_kernel<3,16,8,float>",
+                                              "persistent_kernel<3,16,8,float,false,true>"],
     "persistent_kernel_ff_sedov128.md": ["persistent_kernel<3,16,16,dw>"],
     "persistent_kernel_rk2_sedov128.md": ["persistent_kernel<3,16,16,rd,true>"],
+    "fused_kernel_sedov128.md": ["fused_kernel<3,16,16,rd,false>", "fused_kernel<3,16,16,float,false>",
+                                 "fused_kernel<3,16,16,rd,true>"],
 }
 
 
