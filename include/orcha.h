@@ -517,7 +517,8 @@ ORCHA_API orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, doubl
 
 /* Diagnostics: the FP64 pipe's throughput on the current device, in lane
  * operations per second (one FMA, add or multiply = one operation): op 0
- * FMA, 1 add, 2 multiply. Every SM runs its maximum resident warps, each
+ * FMA, 1 add, 2 multiply, 3 an add issued as an FMA with a run-time 1.0,
+ * 4 a multiply issued as an FMA with a run-time -0.0 (the same bits). Every SM runs its maximum resident warps, each
  * thread eight independent chains of the operation; best of five timed
  * launches after one warm-up (about 0.1 s each). This is the ceiling of the
  * FP64 hydro task, which the FP64 pipe bounds on this GPU (the task's

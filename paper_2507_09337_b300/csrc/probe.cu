@@ -17,8 +17,13 @@ namespace {
 constexpr int kChains = 8;
 constexpr int kThreads = 256;
 
+// OP 0 FMA, 1 add, 2 multiply; 3 an add issued as an FMA (a * one + b, one =
+// 1.0 passed at run time so no compiler can fold it), 4 a multiply issued as
+// an FMA (a * b + mzero, mzero = -0.0 at run time): both give the add's and
+// the multiply's bits exactly.
 template <int OP>
-__global__ void __launch_bounds__(kThreads) fp64_rate_kernel(double* sink, int iters, double b, double c) {
+__global__ void __launch_bounds__(kThreads) fp64_rate_kernel(double* sink, int iters, double b, double c, double one,
+                                                             double mzero) {
     double a[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = 1.0 + 1e-6 * (double)(threadIdx.x + 7 * k);
@@ -27,7 +32,9 @@ __global__ void __launch_bounds__(kThreads) fp64_rate_kernel(double* sink, int i
         for (int k = 0; k < kChains; ++k) {
             if (OP == 0) a[k] = fma(a[k], b, c);
             else if (OP == 1) a[k] = __dadd_rn(a[k], b);
-            else a[k] = __dmul_rn(a[k], b);
+            else if (OP == 2) a[k] = __dmul_rn(a[k], b);
+            else if (OP == 3) a[k] = fma(a[k], one, b);
+            else a[k] = fma(a[k], b, mzero);
         }
     }
     double s = 0.0;
@@ -39,12 +46,16 @@ __global__ void __launch_bounds__(kThreads) fp64_rate_kernel(double* sink, int i
 }  // namespace
 
 extern "C" orcha_status orcha_measure_fp64_rate(int32_t op, double* lane_ops_per_s) {
-    if (!lane_ops_per_s || op < 0 || op > 2)
-        return orcha::set_error(ORCHA_ERR_INVALID, "measure_fp64_rate: op must be 0, 1 or 2 and the output non-null");
+    if (!lane_ops_per_s || op < 0 || op > 4)
+        return orcha::set_error(ORCHA_ERR_INVALID, "measure_fp64_rate: op must be 0 .. 4 and the output non-null");
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    auto kern = op == 0 ? fp64_rate_kernel<0> : op == 1 ? fp64_rate_kernel<1> : fp64_rate_kernel<2>;
+    auto kern = op == 0   ? fp64_rate_kernel<0>
+                : op == 1 ? fp64_rate_kernel<1>
+                : op == 2 ? fp64_rate_kernel<2>
+                : op == 3 ? fp64_rate_kernel<3>
+                          : fp64_rate_kernel<4>;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     if (e != cudaSuccess) return orcha::cuda_error(e, "measure_fp64_rate: device query");
     double* sink = nullptr;
@@ -56,12 +67,12 @@ extern "C" orcha_status orcha_measure_fp64_rate(int32_t op, double* lane_ops_per
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int grid = sms * std::max(1, per_sm), iters = 16384;
     // b slightly below 1 and c small keep every chain finite and normal
-    const double b = op == 1 ? 1e-9 : 0.999999999, c = 1e-9;
+    const double b = (op == 1 || op == 3) ? 1e-9 : 0.999999999, c = 1e-9;
     double best_ms = 1e300;
     for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {    // rep 0 warms up
         e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) {
-            kern<<<grid, kThreads, 0, st>>>(sink, iters, b, c);
+            kern<<<grid, kThreads, 0, st>>>(sink, iters, b, c, 1.0, -0.0);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
