@@ -51,20 +51,20 @@ BYTES_PER_ZONE_3D = 80        # read U^n and write U^{n+1}: 5 vars x 8 B x 2
 FP64_PEAK_TFLOPS = 148 * 2 * 2.032e9 / 1e12    # 2 FP64 lanes / SM / clock at 2032 MHz, non-FMA ops
 
 
-KERNEL_SOURCES = ["paper_2507_09337_b300/csrc/common.cuh", "paper_2507_09337_b300/csrc/hydro.cuh",
-                  "paper_2507_09337_b300/csrc/persistent.cuh", "paper_2507_09337_b300/csrc/dword.cuh",
-                  "paper_2507_09337_b300/csrc/softfp64.cuh", "paper_2507_09337_b300/csrc/fused.cuh",
-                  "paper_2507_09337_b300/csrc/amr.cu"]
+# the headers every hydro kernel is compiled from; a summary adds the files of
+# its own kernels (fused.cuh, amr.cu) on a `kernel_sources:` line
+KERNEL_SOURCES = ["common.cuh", "hydro.cuh", "persistent.cuh", "dword.cuh", "softfp64.cuh"]
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the kernel sources' code: comments and whitespace are
-    removed first, so editing a comment does not void a recorded capture."""
+def kernel_source_hash(extra=()) -> str:
+    """sha256 over the code of KERNEL_SOURCES plus `extra` (file names under
+    csrc/): comments and whitespace are removed first, so editing a comment
+    does not void a recorded capture."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        src = open(os.path.join(ROOT, f)).read()
+    for f in list(KERNEL_SOURCES) + list(extra):
+        src = open(os.path.join(ROOT, "paper_2507_09337_b300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
@@ -75,22 +75,26 @@ def profiled_traffic(profile_md: str, kernel: str):
     """DRAM bytes per launch from a committed ncu summary, or None if the
     summary covers no capture of this kernel variant or the kernel code
     changed since the captures (hash mismatch). The summary's indented
-    machine-readable lines hold one kernel_source_sha256 and one or more
-    `kernel:` lines, each followed by its traffic_bytes_per_launch."""
+    machine-readable lines hold one kernel_source_sha256, optionally one
+    `kernel_sources:` line (comma-separated extra files the hash covers),
+    and one or more `kernel:` lines, each followed by its
+    traffic_bytes_per_launch."""
     path = os.path.join(ROOT, "profiles", profile_md)
     if not os.path.exists(path):
         return None
-    sha, traffic, current = None, {}, None
+    sha, extra, traffic, current = None, (), {}, None
     for line in open(path):
         if ":" in line and line.startswith("    "):
             k, v = (t.strip() for t in line.strip().split(":", 1))
             if k == "kernel_source_sha256":
                 sha = v
+            elif k == "kernel_sources":
+                extra = tuple(t.strip() for t in v.split(",") if t.strip())
             elif k == "kernel":
                 current = v
             elif k == "traffic_bytes_per_launch" and current is not None:
                 traffic[current] = float(v)
-    if sha != kernel_source_hash():
+    if sha != kernel_source_hash(extra):
         return None
     return traffic.get(kernel)
 
@@ -397,13 +401,15 @@ def run_amr(args):
                             "hydro of every leaf, flux correction, restriction, dt"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak, "traffic": None, "ops_per_zone_update": FLOPS_PER_ZONE_3D,
-                     "kernel": "whole two-level step (hydro_kernel<3,16,16,rd,false,false,FluxRegIO> dominant)",
+                     "kernel": "whole two-level step (amr_hydro_kernel<3,16,16> dominant)",
                      "peak_source": "measured FP64 FMA throughput probe (orcha_measure_fp64_rate)"},
         "clocks": clk,
         "e2e": {"value": e2e, "unit": "zone-updates/s", "h2d_bytes_per_step": int(U0.nbytes + U1.nbytes),
                 "d2h_bytes_per_step": int(U0.nbytes + U1.nbytes),
                 "api": "orcha_amr_load(host) + orcha_amr_advance + orcha_amr_store(host), wall clock"},
-        "gpu_launches": len(events) * 9,
+        # per step: coarse guard fill, fine guard fill, hydro of both levels,
+        # flux correction, restriction, two signal-speed launches, dt reduction
+        "gpu_launches": len(events) * 8,
     }
     if not args.no_cpu_baseline:
         import oracle

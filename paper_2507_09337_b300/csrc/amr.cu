@@ -8,8 +8,8 @@
 //   restrict   parents <- the average of their children (current buffers);
 //   guards     coarse: the uniform guard fill (parents included); fine: from
 //              the fine blocks, or the containing coarse cell (injection);
-//   hydro      every coarse leaf and every fine block (the packet kernel,
-//              recording the fluxes through each block's faces);
+//   hydro      every coarse leaf and every fine block in one launch (the
+//              packet sweep, recording the fluxes through each block's faces);
 //   reflux     coarse leaf cells next to a refined block take the average of
 //              the fine fluxes through their face instead of their own;
 //   restrict   parents of the new coarse state;
@@ -169,30 +169,58 @@ __global__ void amr_reflux_kernel(const MeshDev c, const RefluxEntry* __restrict
     }
 }
 
+// One level's part of the hydro launch: its view, its blocks, its buffers
+// (by current buffer) and its flux registers.
+struct AmrLevel {
+    MeshDev m;
+    const int* ids;
+    const double* Uin;
+    double* Uout;
+    double* reg;
+};
+
+// Both levels' blocks in one launch (so one partial last wave, not two): the
+// first n0 x tiles CTAs take the coarse leaves, the rest the fine blocks;
+// every CTA runs the FP64 MUSCL-Hancock step of one block's column tile with
+// its guards from the padded block and records the block's face fluxes.
 template <int NDIM, int TX, int TY>
-cudaError_t launch_hydro_reg_t(const MeshDev& m, const int* ids, int n, const double* Uin, double* Uout, double* reg,
-                               int fsz, cudaStream_t st) {
+__global__ void __launch_bounds__(Tile<NDIM, TX, TY>::template nb<rd, false>())
+amr_hydro_kernel(const AmrLevel* __restrict__ lv, int n0, int tiles_x, int tiles_y, int fsz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long red[32];
+    const int ntile = tiles_x * tiles_y;
+    const int b = blockIdx.x / ntile, tile = blockIdx.x % ntile;
+    const bool fine = b >= n0;
+    const AmrLevel& L = lv[fine ? 1 : 0];
+    FluxRegIO io;
+    io.reg = L.reg;
+    io.fsz = fsz;
+    hydro_tile<NDIM, TX, TY, rd, false, false, false, FluxRegIO>(L.m, L.ids[fine ? b - n0 : b], (tile % tiles_x) * TX,
+                                                                 (tile / tiles_x) * TY, L.Uin, L.Uout, smem_raw, red,
+                                                                 0, -1, 0, io);
+}
+
+template <int NDIM, int TX, int TY>
+cudaError_t launch_amr_hydro_t(const AmrLevel* lv, int n0, int n1, int tiles_x, int tiles_y, int fsz,
+                               cudaStream_t st) {
     using Tl = Tile<NDIM, TX, TY>;
     const size_t smem = Tl::template smem_bytes<double>();
-    auto kern = hydro_kernel<NDIM, TX, TY, rd, false, false, FluxRegIO>;
+    auto kern = amr_hydro_kernel<NDIM, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    FluxRegIO io;
-    io.reg = reg;
-    io.fsz = fsz;
-    const int tx = m.bs[0] / TX, ty = m.bs[1] / TY;
-    kern<<<dim3((unsigned)(n * tx * ty)), dim3(Tl::template nb<rd, false>()), smem, st>>>(m, ids, tx, ty, Uin, Uout, 0,
-                                                                                           io);
+    kern<<<dim3((unsigned)((n0 + n1) * tiles_x * tiles_y)), dim3(Tl::template nb<rd, false>()), smem, st>>>(
+        lv, n0, tiles_x, tiles_y, fsz);
     return cudaGetLastError();
 }
 
-// One FP64 MUSCL-Hancock step of the packet blocks ids[0..n) that also fills
-// their flux registers.
-cudaError_t launch_hydro_reg(const MeshDev& m, int tx, int ty, const int* ids, int n, const double* Uin, double* Uout,
-                             double* reg, int fsz, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+// One FP64 MUSCL-Hancock step of the n0 coarse leaves and the n1 fine blocks
+// of lv[0] and lv[1], filling their flux registers.
+cudaError_t launch_amr_hydro(int ndim, const int bs[3], int tx, int ty, const AmrLevel* lv, int n0, int n1, int fsz,
+                             cudaStream_t st) {
+    if (n0 + n1 <= 0) return cudaSuccess;
+    const int ntx = bs[0] / tx, nty = bs[1] / ty;
 #define ORCHA_R(ND, X, Y) \
-    if (m.ndim == ND && tx == X && ty == Y) return launch_hydro_reg_t<ND, X, Y>(m, ids, n, Uin, Uout, reg, fsz, st);
+    if (ndim == ND && tx == X && ty == Y) return launch_amr_hydro_t<ND, X, Y>(lv, n0, n1, ntx, nty, fsz, st);
     ORCHA_R(3, 16, 16) ORCHA_R(3, 16, 8) ORCHA_R(3, 8, 8) ORCHA_R(2, 16, 16) ORCHA_R(2, 16, 8) ORCHA_R(2, 8, 8)
 #undef ORCHA_R
     return cudaErrorInvalidConfiguration;
@@ -216,6 +244,7 @@ struct orcha_amr {
     double* reg1 = nullptr;               // and of the fine blocks
     orcha::RefluxEntry* reflux_dev = nullptr;
     int nreflux = 0;
+    orcha::AmrLevel* levels_dev = nullptr; // [current buffer][coarse, fine]
     double* staging = nullptr;            // host load/store staging
 };
 
@@ -249,6 +278,7 @@ orcha_status orcha_amr_destroy(orcha_amr* a) {
     cudaFree(a->reg0);
     cudaFree(a->reg1);
     cudaFree(a->reflux_dev);
+    cudaFree(a->levels_dev);
     cudaFree(a->staging);
     orcha_mesh_destroy(a->coarse);
     delete a;
@@ -348,6 +378,19 @@ orcha_status orcha_amr_create(const orcha_mesh_desc* desc, const int32_t* refine
     }
     a->md0.smax = a->smax;
     a->md1.smax = a->smax + nblk0;
+    // the hydro launch's per-level arguments, for either current buffer
+    orcha::AmrLevel lv[2][2];
+    for (int cur = 0; cur < 2; ++cur) {
+        lv[cur][0] = {a->md0, a->leaves_dev, desc->state_dev[cur], desc->state_dev[cur ^ 1], a->reg0};
+        lv[cur][1] = {a->md1, a->fine_ids_dev, a->fine[cur], a->fine[cur ^ 1], a->reg1};
+    }
+    e = cudaMalloc(&a->levels_dev, sizeof(lv));
+    if (e == cudaSuccess) e = cudaMemcpy(a->levels_dev, lv, sizeof(lv), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        orcha_status st = amr_fail(e, "amr_create");
+        orcha_amr_destroy(a);
+        return st;
+    }
     *out = a;
     return ORCHA_OK;
 }
@@ -424,7 +467,6 @@ orcha_status orcha_amr_advance(orcha_amr* a, int32_t nsteps, int32_t init_dt, vo
         double* Uc = a->coarse->desc.state_dev[cur];
         double* Uc1 = a->coarse->desc.state_dev[cur ^ 1];
         double* Uf = a->fine[cur];
-        double* Uf1 = a->fine[cur ^ 1];
         e = orcha::launch_guard_fill(c, a->all_coarse_dev, nblk0, Uc, st);
         if (e == cudaSuccess && a->nfine) {
             orcha::amr_guard_fill_kernel<<<dim3(ggrid, (unsigned)a->nfine), 256, 0, st>>>(
@@ -432,9 +474,7 @@ orcha_status orcha_amr_advance(orcha_amr* a, int32_t nsteps, int32_t init_dt, vo
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)
-            e = orcha::launch_hydro_reg(c, a->tx, a->ty, a->leaves_dev, a->nleaf, Uc, Uc1, a->reg0, a->fsz, st);
-        if (e == cudaSuccess)
-            e = orcha::launch_hydro_reg(a->md1, a->tx, a->ty, a->fine_ids_dev, a->nfine, Uf, Uf1, a->reg1, a->fsz, st);
+            e = orcha::launch_amr_hydro(nd, c.bs, a->tx, a->ty, a->levels_dev + 2 * cur, a->nleaf, a->nfine, a->fsz, st);
         if (e == cudaSuccess && a->nreflux) {
             orcha::amr_reflux_kernel<<<(unsigned)a->nreflux, 256, 0, st>>>(c, a->reflux_dev, a->child0_dev, a->reg0,
                                                                          a->reg1, a->fsz, Uc1);
@@ -445,7 +485,6 @@ orcha_status orcha_amr_advance(orcha_amr* a, int32_t nsteps, int32_t init_dt, vo
         cur ^= 1;
         a->coarse->cur = cur;
     }
-    (void)nd;
     if (e != cudaSuccess) return amr_fail(e, "amr_advance");
     return ORCHA_OK;
 }
