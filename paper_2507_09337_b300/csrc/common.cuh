@@ -345,12 +345,14 @@ __device__ __forceinline__ ff ff_scale(ff d, float ch, float cl) {
     const float pe = fmaf(d.hi, ch, -p);                  // d.hi * ch = p + pe exactly
     return {p, fmaf(d.hi, cl, fmaf(d.lo, ch, pe))};
 }
-// (a.hi + a.lo) + (b.hi + b.lo), renormalised.
+// (a.hi + a.lo) + (b.hi + b.lo) without renormalising: the high parts'
+// sum exactly (two_sum) and the low parts added to its error. The pair may
+// be an ulp or so off normalised, which its uses do not need: another such
+// sum, or ff_to_double, whose one FP64 addition rounds hi + lo, the same
+// real number a renormalised pair would hold.
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
     const ff s = two_sum(a.hi, b.hi);
-    const float lo = s.lo + (a.lo + b.lo);
-    const float hi = s.hi + lo;
-    return {hi, lo - (hi - s.hi)};
+    return {s.hi, s.lo + (a.lo + b.lo)};
 }
 // Exact difference a - b of two floats as a float-float.
 __device__ __forceinline__ ff ff_diff(float a, float b) { return two_sum(a, -b); }

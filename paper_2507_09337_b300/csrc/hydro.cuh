@@ -392,6 +392,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     const double* Ub = Uin + (long long)blk * m.blk_stride;
     double* Ob = Uout + (long long)blk * m.blk_stride;
     const int bz = (NDIM == 3) ? m.bs[2] : 1;
+    const int lgbz = 31 - __clz(bz);     // block sizes are 8, 16 or 32 (1 in 2D): bz = 2^lgbz
     if (NDIM != 3 || z1 < 0) { z0 = 0; z1 = bz; }
     const int bc[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
 
@@ -541,12 +542,14 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         }
         int sbz = bc[2], sz = pzi + kGuard;
         if (GATHER && (pzi < 0 || pzi >= bz)) {
-            const int n = m.nb[2] * m.bs[2];
-            int gi = bc[2] * m.bs[2] + pzi;
-            if (m.periodic[2]) { gi %= n; gi = gi < 0 ? gi + n : gi; }
+            // a sweep's planes reach at most four past the ends of its column
+            // (pass A of a fused sweep), so one wrap suffices
+            const int n = m.nb[2] * bz;
+            int gi = bc[2] * bz + pzi;
+            if (m.periodic[2]) gi = gi < 0 ? gi + n : (gi >= n ? gi - n : gi);
             else gi = gi < 0 ? 0 : (gi > n - 1 ? n - 1 : gi);
-            sbz = gi / m.bs[2];
-            sz = gi % m.bs[2] + kGuard;
+            sbz = gi >> lgbz;
+            sz = (gi & (bz - 1)) + kGuard;
         }
         zb = sbz * nbxy;
         zc = sz * plane;
@@ -934,7 +937,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             }
             if (p >= z0 + 1) {
                 // plane q of the column: block qb above blk, in-block plane ql
-                const int q = p - 1, qb = q / bz, ql = q - qb * bz;
+                const int q = p - 1, qb = q >> lgbz, ql = q & (bz - 1);
                 if (owner) {
                     const long long gi = (long long)qb * nbxy * m.blk_stride +
                                          ((long long)(ql + kGuard) * py + (y0 + tj + kGuard)) * px + (x0 + ti + kGuard);
