@@ -529,6 +529,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     // slot of plane pzi in the three-plane ring; planes run from -2 (from -4
     // in pass A of a fused sweep), and % of a negative number is negative
     auto ring_slot = [](int pzi) -> int { return (pzi + 6) % 3; };
+    int slot_m = 0, slot_c = 0, slot_p = 0;     // ring slots of planes p - 1, p, p + 1 (3D), rotated per plane
 
     // z part of the source of plane pzi (interior z index, -2 .. bz+1; 2D: 0):
     // the block-index offset (zb) and the in-block cell offset (zc)
@@ -575,9 +576,8 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             }
         }
     };
-    // L: primitives of plane pzi into its ring slot
-    auto load_plane = [&](int pzi) {
-        const int slot = (NDIM == 3) ? ring_slot(pzi) : 0;
+    // L: primitives of plane pzi into ring slot `slot`
+    auto load_plane = [&](int pzi, int slot) {
         S* w = sW + slot * NW * R2N;
         int zb, zc;
         plane_z(pzi, zb, zc);
@@ -646,8 +646,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     using A2 = Arith<T, 2>;      // arithmetic type of the predictor
     auto predict_core = [&](int pzi, int c2, A2 (&Wc)[NV], A2 (&dW)[3][NV], A2 (&Wb)[NV]) {
         using A = A2;
-        const int sc = (NDIM == 3) ? ring_slot(pzi) : 0;
-        const S* w = sW + sc * NW * R2N;
+        const S* w = sW + slot_c * NW * R2N;
 #pragma unroll
         for (int v = 0; v < NV; ++v) Wc[v] = as<A>(P<T>::ld(&w[v * R2N + c2]));
         const A rc = as<A>(P<T>::ld(&w[NV * R2N + c2]));
@@ -659,8 +658,8 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
             if (d == 0) { cm = c2 - 1; cp = c2 + 1; wm = w; wp = w; }
             else if (d == 1) { cm = c2 - R2X; cp = c2 + R2X; wm = w; wp = w; }
             else {
-                wm = sW + ring_slot(pzi - 1) * NW * R2N;
-                wp = sW + ring_slot(pzi + 1) * NW * R2N;
+                wm = sW + slot_m * NW * R2N;
+                wp = sW + slot_p * NW * R2N;
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -835,17 +834,25 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     const int pbeg = (NDIM == 3) ? z0 - 1 : 0, pend = (NDIM == 3) ? z1 : 0;
     if (NDIM == 3) {
         if (Prefetch<T>::value) { prefetch_plane(z0 - 1); prefetch_plane(z0); }
-        load_plane(z0 - 2);
-        load_plane(z0 - 1);
+        slot_m = ring_slot(z0 - 2);
+        slot_c = ring_slot(z0 - 1);
+        slot_p = ring_slot(z0);
+        load_plane(z0 - 2, slot_m);
+        load_plane(z0 - 1, slot_c);
     }
 
     for (int p = pbeg; p <= pend; ++p) {
+        if (NDIM == 3) {
+            slot_m = ring_slot(p - 1);
+            slot_c = ring_slot(p);
+            slot_p = ring_slot(p + 1);
+        }
         const bool inner = p >= z0 && p < z1;      // plane p is updated here: it has x/y faces to flux
         if (NDIM == 3) {
             if (Prefetch<T>::value && p < pend) prefetch_plane(p + 2);   // planes up to pend + 1 are loaded
-            load_plane(p + 1);
+            load_plane(p + 1, slot_p);
         }
-        else load_plane(0);
+        else load_plane(0, 0);
         __syncthreads();
 
         // ---- P: predict
@@ -881,35 +888,35 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         // ---- F: x and y face fluxes of plane p
         if (inner) {
             for (int f = member ? tid : Tl::NXF + Tl::NYF; f < Tl::NXF + Tl::NYF; f += NB) {
-                int iL, iR, fL, fR, nrm;
-                if (f < Tl::NXF) {
+                // the face's left state (face array x+ or y+, where its flux
+                // goes too) and right state (x- or y-), and the slots of the
+                // normal and first tangential velocity: (rho, u_n, u_t..., p)
+                const bool ynrm = f >= Tl::NXF;
+                S* pl;
+                const S* pr;
+                int on, ot;
+                if (!ynrm) {
                     const int fi = f % (TX + 1), fj = f / (TX + 1);
-                    iL = (fj + 1) * R1X + fi; iR = iL + 1; fL = 1; fR = 0; nrm = 0;
+                    pl = sGx + (fj + 1) * R1X + fi;
+                    pr = pl - (NV * R1N - 1);
+                    on = R1N; ot = 2 * R1N;
                 } else {
                     const int f2 = f - Tl::NXF;
                     const int fi = f2 % TX, fj = f2 / TX;
-                    iL = fj * R1X + fi + 1; iR = iL + R1X; fL = 3; fR = 2; nrm = 1;
+                    pl = sGy + fj * R1X + fi + 1;
+                    pr = pl - (NV * R1N - R1X);
+                    on = 2 * R1N; ot = R1N;
                 }
                 T L[NV], R[NV], F[NV];
-                // normal-first order: (rho, u_n, u_t..., p)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    int src = v;
-                    if (v == 1) src = 1 + nrm;
-                    else if (v == 2 && nrm == 1) src = 1;
-                    L[v] = P<T>::ld(&sFS[(fL * NV + src) * R1N + iL]);
-                    R[v] = P<T>::ld(&sFS[(fR * NV + src) * R1N + iR]);
+                    const int o = v == 1 ? on : (v == 2 ? ot : v * R1N);
+                    L[v] = P<T>::ld(pl + o);
+                    R[v] = P<T>::ld(pr + o);
                 }
                 hll<T, NDIM, false>(L, R, F, g, igm1);
-                S* dst = ((nrm == 0) ? sGx : sGy) + iL;
-                const int stride = R1N;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    int dv = v;
-                    if (v == 1) dv = 1 + nrm;
-                    else if (v == 2 && nrm == 1) dv = 1;
-                    P<T>::st(&dst[dv * stride], F[v]);
-                }
+                for (int v = 0; v < NV; ++v) P<T>::st(pl + (v == 1 ? on : (v == 2 ? ot : v * R1N)), F[v]);
             }
         }
         __syncthreads();
