@@ -515,6 +515,22 @@ ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t se
  * sqrt(x / rho) (relative). Synchronous. Errors: INVALID, CUDA. */
 ORCHA_API orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, double max_err[6]);
 
+/* Diagnostics: the persistent one-step tasks skip the FP64 signal speed of a
+ * cell whose FP32 upper bound lies below a quarter of the previous step's
+ * largest speed (the dt rule CFL / max_cells sum_d (|u_d| + c) / dx_d needs
+ * only the maximum; the step's reducer re-evaluates in FP64 whenever a
+ * skipped bound could exceed it, so dt keeps its bits). This checks the
+ * bound against the FP64 speed on `count` pseudo-random 3D states derived
+ * from `seed` (densities 2^-20 .. 2^20, speeds up to 10^6, pressures down to
+ * 10^-14 of the kinetic energy density): counts[0] = states where the bound
+ * applied but lies below the FP64 speed (0 when the bound is sound),
+ * counts[1] = states where it applied, counts[2] = states where it applied
+ * although the FP64 evaluation finds the state non-physical (0 when sound);
+ * *max_ratio = the largest bound / speed ratio. Synchronous. Errors:
+ * INVALID, CUDA. No counterpart in the paper (a check of this build's
+ * arithmetic). */
+ORCHA_API orcha_status orcha_selftest_speed_bound(uint64_t count, uint64_t seed, uint64_t counts[3], double* max_ratio);
+
 /* Diagnostics: the FP64 pipe's throughput on the current device, in lane
  * operations per second (one FMA, add or multiply = one operation): op 0
  * FMA, 1 add, 2 multiply, 3 an add issued as an FMA with a run-time 1.0,

@@ -152,6 +152,8 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_fp64_emulation": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "orcha_selftest_dword": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "orcha_selftest_speed_bound": (_st, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "orcha_measure_fp64_rate": (_st, [_i32, ctypes.POINTER(ctypes.c_double)]),
     "orcha_amr_fine_elems": (ctypes.c_size_t, [ctypes.POINTER(orcha_mesh_desc), _i32]),
     "orcha_amr_create": (_st, [ctypes.POINTER(orcha_mesh_desc), ctypes.POINTER(_i32), _i32, _vp, _vp,
@@ -365,6 +367,16 @@ def orcha_selftest_dword(count: int, seed: int = 1) -> list:
     err = (ctypes.c_double * 6)()
     _check(lib().orcha_selftest_dword(int(count), int(seed), err))
     return list(err)
+
+
+def orcha_selftest_speed_bound(count: int, seed: int = 1) -> tuple:
+    """(states where the bound lies below the FP64 speed, states where it
+    applied, states where it applied to a non-physical state, largest
+    bound / speed ratio)."""
+    counts = (ctypes.c_uint64 * 3)()
+    ratio = ctypes.c_double()
+    _check(lib().orcha_selftest_speed_bound(int(count), int(seed), counts, ctypes.byref(ratio)))
+    return counts[0], counts[1], counts[2], ratio.value
 
 
 def orcha_measure_fp64_rate(op: int = 0) -> float:

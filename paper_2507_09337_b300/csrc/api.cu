@@ -450,6 +450,7 @@ orcha_status orcha_batch_destroy(orcha_batch* b) {
         cudaFree(l.done_dev);
         cudaFree(l.scratch);
         cudaFree(l.smax2);
+        cudaFree(l.sub);
     }
     cudaFree(b->queue);
     cudaFree(b->cur_dev);
@@ -590,6 +591,18 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
                 sl[i].smax2 = L.smax2 + off;
                 off += b->meshes[i]->nblk;
             }
+        }
+    }
+    if (!fused && e == cudaSuccess) {
+        // one-step variants: the signal-speed filter's per-block bounds (hydro.cuh, SpeedBound)
+        long long nb_all = 0;
+        for (auto* m : b->meshes) nb_all += m->nblk;
+        e = cudaMalloc(&L.sub, sizeof(unsigned long long) * (size_t)nb_all);
+        if (e == cudaSuccess) e = cudaMemset(L.sub, 0, sizeof(unsigned long long) * (size_t)nb_all);
+        long long off = 0;
+        for (size_t i = 0; i < ns; ++i) {
+            sl[i].m.sub = L.sub + off;
+            off += b->meshes[i]->nblk;
         }
     }
     if (e == cudaSuccess) e = cudaMalloc(&L.slots_dev, sizeof(orcha::SlotDev) * ns);
@@ -741,6 +754,21 @@ orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, double max_err[
     cudaFree(err);
     if (e != cudaSuccess) return cuda_fail(e, "selftest");
     for (int k = 0; k < 6; ++k) std::memcpy(&max_err[k], &h[k], sizeof(double));
+    return ORCHA_OK;
+}
+
+orcha_status orcha_selftest_speed_bound(uint64_t count, uint64_t seed, uint64_t counts[3], double* max_ratio) {
+    if (!counts || !max_ratio) return fail(ORCHA_ERR_INVALID, "selftest: null argument");
+    unsigned long long* res = nullptr;
+    ORCHA_CUDA(cudaMalloc(&res, 5 * sizeof(unsigned long long)), "selftest alloc");
+    cudaError_t e = cudaMemset(res, 0, 5 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = orcha::launch_selftest_speed_bound(count, seed, res, nullptr);
+    unsigned long long h[4] = {};
+    if (e == cudaSuccess) e = cudaMemcpy(h, res, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(res);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    for (int k = 0; k < 3; ++k) counts[k] = h[k];
+    std::memcpy(max_ratio, &h[3], sizeof(double));
     return ORCHA_OK;
 }
 

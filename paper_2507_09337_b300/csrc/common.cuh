@@ -372,7 +372,25 @@ struct MeshDev {
     const double* dt;       // device: current time step
     unsigned long long* smax;   // device: per-block largest signal speed (bits of a non-negative double)
     int* err;               // device: error word (ORCHA_DEVERR_* bits)
+    // device, or null: per-block largest FP32 upper bound of the signal speeds
+    // the step skipped (bits of a non-negative double; see SpeedBound in
+    // hydro.cuh). Null: every cell's speed is evaluated in FP64.
+    unsigned long long* sub = nullptr;
 };
+
+// |x| rounded toward zero to binary32, on the integer pipe: f <= |x| <
+// f (1 + 2^-23). True when x is 0 or 2^-40 <= |x| < 2^41, the range in which
+// the signal-speed bound below keeps every FP32 intermediate normal; false
+// otherwise (f is then meaningless). The top 23 fraction bits of the binary64
+// pattern are the binary32 fraction; the 9 low exponent bits plus 128 (mod
+// 512) are the binary32 biased exponent e - 896 for e in that range.
+__device__ __forceinline__ bool mag_f32_rz(double x, float& f) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32) & 0x7FFFFFFFu, lo = (unsigned)b;
+    f = __uint_as_float(__funnelshift_l(lo, hi, 3) + 0x40000000u);
+    if ((hi | lo) == 0u) f = 0.0f;
+    return (hi >> 20) - 983u <= 80u || (hi | lo) == 0u;
+}
 
 // Largest of two non-negative doubles given as bit patterns (NaN patterns of
 // either sign compare above every finite value, so a NaN is never lost).
@@ -398,6 +416,23 @@ __device__ __forceinline__ void cta_raise_smax(double s, unsigned long long* scr
         unsigned long long m = 0;
         for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = umax64(m, scratch[w]);
         atomicMax(dst, m);
+    }
+}
+
+// The same for two values at once (one barrier): a into dst, b into dst2.
+// Needs at most 16 warps (scratch holds 32 words).
+__device__ __forceinline__ void cta_raise_smax2(unsigned long long a, unsigned long long b, unsigned long long* scratch,
+                                                unsigned long long* dst, unsigned long long* dst2) {
+    a = warp_max_u64(a);
+    b = warp_max_u64(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { scratch[warp] = a; scratch[16 + warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ma = 0, mb = 0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) { ma = umax64(ma, scratch[w]); mb = umax64(mb, scratch[16 + w]); }
+        atomicMax(dst, ma);
+        if (mb) atomicMax(dst2, mb);
     }
 }
 

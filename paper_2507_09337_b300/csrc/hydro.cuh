@@ -176,7 +176,9 @@ __device__ __forceinline__ void hll(const T* L, const T* R, T* F, T g, T igm1) {
 // block `blk` of the padded state U handled by this thread (stride
 // blockDim.x), as the bits of a non-negative double; flags non-physical cells.
 // (chunk, nchunks): this CTA takes cells chunk * blockDim.x + t, stepping
-// nchunks * blockDim.x.
+// nchunks * blockDim.x. CG: load through L2 only (__ldcg), for a state other
+// CTAs of the same launch have just written.
+template <bool CG = false>
 __device__ __forceinline__ unsigned long long block_signal_speed(const MeshDev& m, int blk,
                                                                  const double* __restrict__ U, int chunk = 0,
                                                                  int nchunks = 1) {
@@ -188,7 +190,7 @@ __device__ __forceinline__ unsigned long long block_signal_speed(const MeshDev& 
         const int kk = (m.ndim == 3) ? k + kGuard : 0;
         const int po = (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
         rd Uc[5], W[5], r;
-        for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(Ub[po + v * m.var_stride]);
+        for (int v = 0; v < m.nvar; ++v) Uc[v] = rd(CG ? __ldcg(&Ub[po + v * m.var_stride]) : Ub[po + v * m.var_stride]);
         if (m.ndim == 3) prim_from_cons<rd, 3>(Uc, W, r, rd(m.gm1));
         else prim_from_cons<rd, 2>(Uc, W, r, rd(m.gm1));
         const int nv = m.nvar;
@@ -234,6 +236,86 @@ __device__ __forceinline__ unsigned long long new_state_speed(const MeshDev& m, 
 #pragma unroll
     for (int d = 1; d < NDIM; ++d) s = s + ((rd(fabs(W[1 + d].v)) + c) * rd(m.idx[d]));
     return (unsigned long long)bits(s);   // s >= 0 or NaN
+}
+
+// ---------------------------------------------------------------- signal-speed filter
+// Only the largest signal speed of a step matters (dt = cfl / max), and on
+// most meshes nearly every cell lies far below it. The FP64 evaluation
+// (new_state_speed<rd>: a reciprocal, a square root and ~20 more FP64-pipe
+// operations) is therefore skipped for a cell whose rigorous FP32 upper
+// bound lies below a threshold, a quarter of the previous step's maximum
+// (cfl / (4 dt)); the bound is raised into the block's `sub` entry instead.
+// The step's reducer accepts max smax as the exact maximum only when no
+// skipped bound exceeds it, and otherwise evaluates the cells of the blocks
+// whose bound does in FP64 (finish_mesh_step). So dt has the bits of the
+// unfiltered evaluation whatever the threshold; the threshold only decides
+// how often the FP64 path runs.
+//
+// The bound: the state's magnitudes rounded toward zero to binary32 (below)
+// and up by one ulp bracket the exact ones; every later operation rounds
+// towards the side it bounds (__fmul_ru and friends, the IEEE directed
+// roundings), so p_hi >= (gamma-1)(E - |m|^2/(2 rho)), c_hi >= sqrt(gamma p /
+// rho) and s_hi >= sum_d (|m_d|/rho + c) / dx_d for the real numbers the
+// double state and constants define. The FP64 evaluation differs from that
+// real value by at most ~2^-23 (1/dx_max / 1/dx_min) of it, even under
+// cancellation in E - |m|^2/(2 rho) (its pressure error is ~2^-50 (E + ke),
+// whose square root is ~2^-25 (c + |u|)); `margin` covers it 16 times over.
+// A cell is skipped only if its FP32 lower bound of p exceeds 2^-40 E, which
+// keeps the FP64 pressure positive too (the non-physical check the FP64 path
+// makes), and only if its values lie in the range mag_f32_rz accepts.
+struct SpeedBound {
+    float gm1_lo, gm1_hi, g_hi, idx_hi[3], margin, thr;
+};
+
+__device__ __forceinline__ SpeedBound speed_bound_setup(const MeshDev& m, double dt) {
+    SpeedBound b;
+    b.gm1_lo = __double2float_rd(m.gm1);
+    b.gm1_hi = __double2float_ru(m.gm1);
+    b.g_hi = __double2float_ru(m.gamma);
+    double imin = m.idx[0], imax = m.idx[0];
+    for (int d = 0; d < 3; ++d) {
+        b.idx_hi[d] = __double2float_ru(m.idx[d]);
+        if (d < m.ndim) { imin = fmin(imin, m.idx[d]); imax = fmax(imax, m.idx[d]); }
+    }
+    b.margin = __fmaf_ru(__double2float_ru(imax / imin), 0x1p-19f, 1.0f);
+    const double t = m.cfl / (4.0 * dt);
+    b.thr = (m.sub != nullptr && t > 0.0 && t < 1e30) ? __double2float_rd(t) : 0.0f;
+    return b;
+}
+
+// An FP32 upper bound ub of the FP64 signal speed of the state Un (the value
+// new_state_speed<rd> returns), or false if the bound does not apply.
+template <int NDIM>
+__device__ __forceinline__ bool speed_upper(const SpeedBound& sb, const rd* Un, float& ub) {
+    constexpr int NV = NDIM + 2;
+    constexpr float kUp = 0x1.000002p0f;                 // 1 + 2^-23: a truncated magnitude times this bounds it
+    float rl, el, ml[NDIM];
+    bool ok = mag_f32_rz(Un[0].v, rl) && mag_f32_rz(Un[NV - 1].v, el) && __double_as_longlong(Un[0].v) > 0 &&
+              __double_as_longlong(Un[NV - 1].v) > 0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) ok = mag_f32_rz(Un[1 + d].v, ml[d]) && ok;
+    if (!ok) return false;
+    const float rh = __fmul_ru(rl, kUp), eh = __fmul_ru(el, kUp);
+    const float ri_hi = __frcp_ru(rl), ri_lo = __frcp_rd(rh);      // bracket 1/rho
+    float kel = 0.0f, keh = 0.0f, ah[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const float mh = __fmul_ru(ml[d], kUp);
+        ah[d] = __fmul_ru(mh, ri_hi);                                // >= |m_d| / rho
+        kel = __fadd_rd(kel, __fmul_rd(ml[d], __fmul_rd(ml[d], ri_lo)));
+        keh = __fadd_ru(keh, __fmul_ru(mh, ah[d]));
+    }
+    kel = 0.5f * kel;                                                // exact halvings (normal range)
+    keh = 0.5f * keh;
+    const float pl = __fmul_rd(sb.gm1_lo, __fadd_rd(el, -keh));
+    if (!(pl > eh * 0x1p-40f)) return false;
+    const float ph = __fmul_ru(sb.gm1_hi, __fadd_ru(eh, -kel));
+    const float ch = __fsqrt_ru(__fmul_ru(__fmul_ru(sb.g_hi, ph), ri_hi));
+    float s = 0.0f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) s = __fadd_ru(s, __fmul_ru(__fadd_ru(ah[d], ch), sb.idx_hi[d]));
+    ub = __fmul_ru(s, sb.margin);
+    return true;
 }
 
 // The FP32-flux shortcut's signal speed (new_state_speed<float>: FP32, rounded
@@ -304,6 +386,7 @@ struct Tile {
 // kThreads: the CTA size of a fused launch (pass A's thread count); a pass
 // with fewer threads idles the rest outside its barriers.
 struct GlobalIO {
+    static constexpr bool kFilter = false;  // skip FP64 signal speeds below the threshold (SpeedBound)
     static constexpr bool kIn = false;      // planes and base values from the scratch
     static constexpr bool kOut = false;     // new values into the scratch
     static constexpr int kRaise = 1;        // 0: none; 1: m.smax (RK: stage 2); 2: the inner cells into io.smax2
@@ -316,7 +399,7 @@ struct GlobalIO {
 };
 template <int NTH, int RAISE>
 struct ScratchOutIO {
-    static constexpr bool kIn = false, kOut = true, kReg = false;
+    static constexpr bool kIn = false, kOut = true, kReg = false, kFilter = false;
     static constexpr int kRaise = RAISE, kThreads = NTH;
     double* scratch;
     unsigned long long* smax2;
@@ -325,7 +408,7 @@ struct ScratchOutIO {
 };
 template <int NTH>
 struct ScratchInIO {
-    static constexpr bool kIn = true, kOut = false, kReg = false;
+    static constexpr bool kIn = true, kOut = false, kReg = false, kFilter = false;
     static constexpr int kRaise = 1, kThreads = NTH;
     double* scratch;
     unsigned long long* smax2;
@@ -339,6 +422,11 @@ struct ScratchInIO {
 // (whole blocks) only.
 struct FluxRegIO : GlobalIO {
     static constexpr bool kReg = true;
+};
+// The one-step task of the persistent path, whose reducer (finish_mesh_step)
+// handles the skipped speeds' bounds: GlobalIO with the signal-speed filter.
+struct FilterIO : GlobalIO {
+    static constexpr bool kFilter = true;
 };
 
 // One column tile of one block: the z sweep over interior planes [z0, z1)
@@ -785,11 +873,25 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
     constexpr bool F32 = std::is_same<T, float>::value && FX;     // float-float flux sums
     using SpeedT = typename std::conditional<F32, float, rd>::type;   // signal-speed rule of the new state
     constexpr bool DW = std::is_same<T, dw>::value;
+    // the signal-speed filter (SpeedBound): FP64 speeds, one-step task only
+    unsigned long long smaxb = 0ull;   // bits of the largest signal speed
+    constexpr bool kFilter = std::is_same<SpeedT, rd>::value && IO::kFilter;
+    const SpeedBound sbf = kFilter ? speed_bound_setup(m, dt) : SpeedBound{};
+    unsigned long long subb = 0ull;    // bits of the largest bound of a skipped cell
+    auto raise_speed = [&](const rd (&Un)[NV]) {
+        if constexpr (kFilter) {
+            float ub;
+            if (sbf.thr > 0.0f && speed_upper<NDIM>(sbf, Un, ub) && ub < sbf.thr) {
+                subb = umax64(subb, (unsigned long long)__double_as_longlong(to_f64(ub)));
+                return;
+            }
+        }
+        smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
+    };
     T zp_prev[NV], Fz_prev[NV];
     double acc_prev[NV];
     ff acc_ff[NV];
     dw acc_dw[NV];
-    unsigned long long smaxb = 0ull;   // bits of the largest signal speed
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         zp_prev[v] = P<T>::zero();
@@ -968,12 +1070,17 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                         if (RK && stage == 2) Un[v] = P<rd>::half(rd((IO::kIn ? Ub : Ob)[gi + v * vs]) + Un[v]);
                         store_new(q, gi, v, Un[v].v);
                     }
-                    if (raise_here(q)) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
+                    if (raise_here(q)) raise_speed(Un);
                 }
                 // leaving a block (or the item's range): raise its signal speed
                 // (CTA-uniform: every thread takes part, non-owners with 0)
                 if (IO::kRaise == 1 && (!RK || stage == 2) && (q == z1 - 1 || ql == bz - 1)) {
-                    cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
+                    if (kFilter && m.sub) {
+                        cta_raise_smax2(smaxb, subb, red, &m.smax[blk + qb * nbxy], &m.sub[blk + qb * nbxy]);
+                        subb = 0ull;
+                    } else {
+                        cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk + qb * nbxy]);
+                    }
                     smaxb = 0ull;
                 }
             }
@@ -1031,13 +1138,15 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
                     if (RK && stage == 2) Un[v] = P<rd>::half(rd((IO::kIn ? Ub : Ob)[gi + v * vs]) + Un[v]);
                     store_new(0, gi, v, Un[v].v);
                 }
-                if (raise_here(0)) smaxb = umax64(smaxb, new_state_speed<SpeedT, NDIM>(m, Un));
+                if (raise_here(0)) raise_speed(Un);
             }
         }
     }
     if constexpr (NDIM == 2) {
-        if (IO::kRaise == 1 && (!RK || stage == 2))
-            cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
+        if (IO::kRaise == 1 && (!RK || stage == 2)) {
+            if (kFilter && m.sub) cta_raise_smax2(smaxb, subb, red, &m.smax[blk], &m.sub[blk]);
+            else cta_raise_smax(__longlong_as_double((long long)smaxb), red, &m.smax[blk]);
+        }
     }
     if constexpr (IO::kRaise == 2) cta_raise_smax(__longlong_as_double((long long)smaxb), red, &io.smax2[blk]);
 }

@@ -401,6 +401,69 @@ __global__ void selftest_dword_kernel(unsigned long long n, unsigned long long s
     for (int k = 0; k < 6; ++k) st_raise(err + k, mx[k]);
 }
 
+// The signal-speed filter's bound (hydro.cuh, speed_upper) against the FP64
+// signal speed it stands for, on pseudo-random 3D states: density 2^-20 ..
+// 2^20, velocities up to 10^6 in any direction, pressures from 10^-14 of the
+// kinetic energy density (heavy cancellation in E - |m|^2/(2 rho)) to 10^6 of
+// it, gamma 1.4 or 5/3, cell widths with aspect ratios up to 4. res[0]:
+// states where the bound applied but lies below the FP64 speed (must be 0);
+// res[1]: states where it applied; res[2]: states where it applied although
+// the FP64 path finds the state non-physical (must be 0); res[3]: the
+// largest bound / speed ratio, as double bits; res[4]: a scratch word for the
+// FP64 path's error flag.
+__global__ void selftest_speed_bound_kernel(unsigned long long n, unsigned long long seed, unsigned long long* res,
+                                            int* err_sink) {
+    unsigned long long bad = 0, applied = 0, nonphys = 0;
+    double worst = 0.0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r1 = mix64(seed + 4 * i), r2 = mix64(seed + 4 * i + 1), r3 = mix64(seed + 4 * i + 2),
+                                 r4 = mix64(seed + 4 * i + 3);
+        auto unit = [](unsigned long long r, int k) { return (double)((r >> (16 * k)) & 0xFFFF) / 65536.0; };
+        MeshDev m{};
+        m.ndim = 3;
+        m.nvar = 5;
+        m.gamma = (r4 & 1) ? 1.4 : 5.0 / 3.0;
+        m.gm1 = m.gamma - 1.0;
+        m.cfl = 0.8;
+        for (int d = 0; d < 3; ++d) m.idx[d] = 64.0 * exp2(2.0 * unit(r4, d) - 1.0) * (1 + (int)((r4 >> 60) & 3));
+        const double rho = exp2(40.0 * unit(r1, 0) - 20.0);
+        double u[3], ke = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double mag = (((r2 >> (8 * d)) & 7) == 0) ? 0.0 : pow(10.0, 12.0 * unit(r1, d + 1) - 6.0);
+            u[d] = ((r3 >> d) & 1) ? -mag : mag;
+            ke += 0.5 * rho * u[d] * u[d];
+        }
+        const double pr = (ke > 0.0) ? ke * pow(10.0, 20.0 * unit(r3, 1) - 14.0) : rho * exp2(20.0 * unit(r3, 2) - 10.0);
+        rd Un[5];
+        Un[0] = rd(rho);
+        for (int d = 0; d < 3; ++d) Un[1 + d] = rd(rho * u[d]);
+        Un[4] = rd(pr / m.gm1 + ke);
+        SpeedBound sb = speed_bound_setup(m, 1.0);
+        float ub;
+        if (!speed_upper<3>(sb, Un, ub)) continue;
+        ++applied;
+        rd W[5], r;
+        prim_from_cons<rd, 3>(Un, W, r, rd(m.gm1));
+        if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[4]))) { ++nonphys; continue; }
+        m.err = err_sink;
+        const double s = __longlong_as_double((long long)new_state_speed<rd, 3>(m, Un));
+        const double b = (double)ub;
+        if (!(b >= s)) ++bad;
+        worst = fmax(worst, b / s);
+    }
+    if (bad) atomicAdd(&res[0], bad);
+    if (applied) atomicAdd(&res[1], applied);
+    if (nonphys) atomicAdd(&res[2], nonphys);
+    atomicMax(&res[3], (unsigned long long)__double_as_longlong(worst));
+}
+
+cudaError_t launch_selftest_speed_bound(unsigned long long n, unsigned long long seed, unsigned long long* res,
+                                        cudaStream_t st) {
+    selftest_speed_bound_kernel<<<148 * 8, 256, 0, st>>>(n, seed, res, reinterpret_cast<int*>(res + 4));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_selftest_dword(unsigned long long n, unsigned long long seed, unsigned long long* err,
                                   cudaStream_t st) {
     selftest_dword_kernel<<<148 * 8, 256, 0, st>>>(n, seed, err);

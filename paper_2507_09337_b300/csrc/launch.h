@@ -128,6 +128,8 @@ cudaError_t launch_selftest_fp64(unsigned long long n, unsigned long long seed, 
                                  cudaStream_t st);
 // Self-test of the double-word arithmetic: raises err[0..5] (bits of
 // non-negative doubles) to the largest errors against FP64 references.
+cudaError_t launch_selftest_speed_bound(unsigned long long n, unsigned long long seed, unsigned long long* res,
+                                        cudaStream_t st);
 cudaError_t launch_selftest_dword(unsigned long long n, unsigned long long seed, unsigned long long* err,
                                   cudaStream_t st);
 // Built column-tile variants, widest first.

@@ -69,8 +69,32 @@ __device__ __forceinline__ unsigned long long cta_max_of(const unsigned long lon
 // set) also checks that its shared dt kept the second step stable:
 // dt * s(intermediate state) <= 1, the limit of the summed-direction rule,
 // else ORCHA_DEVERR_CFL. Called by all threads of one CTA.
+// With the signal-speed filter (sd.m.sub set; hydro.cuh, SpeedBound) the
+// maximum over the exactly evaluated cells is the step's maximum only if no
+// skipped cell's bound exceeds it; otherwise this CTA evaluates the cells of
+// every block whose bound does in FP64 (rare: the maximum fell below a
+// quarter of the previous one) and the result has the unfiltered bits.
 __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned long long* red, bool update_dt) {
-    const unsigned long long t = cta_max_of(sd.m.smax, sd.nblk, red);
+    unsigned long long t = cta_max_of(sd.m.smax, sd.nblk, red);     // valid in thread 0
+    if (sd.m.sub && update_dt) {
+        const unsigned long long u = cta_max_of(sd.m.sub, sd.nblk, red);
+        __shared__ unsigned long long s_tu[2];
+        if (threadIdx.x == 0) { s_tu[0] = t; s_tu[1] = u; }
+        __syncthreads();
+        const unsigned long long tt = s_tu[0];
+        if (s_tu[1] > tt) {                         // CTA-uniform: a skipped bound exceeds the maximum
+            const double* Un = sd.state[__ldcg(sd.cur) ^ 1];
+            unsigned long long b = 0ull;
+            for (int i = 0; i < sd.nblk; ++i)       // every thread reads the same entry: uniform branch
+                if (__ldcg(&sd.m.sub[i]) > tt) b = umax64(b, block_signal_speed<true>(sd.m, i, Un));
+            b = warp_max_u64(b);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t = umax64(t, red[w]);
+        }
+        __syncthreads();
+    }
     const unsigned long long t2 = sd.smax2 ? cta_max_of(sd.smax2, sd.nblk, red) : 0ull;
     if (threadIdx.x == 0) {
         const double s = __longlong_as_double((long long)t);
@@ -86,6 +110,8 @@ __device__ __forceinline__ void finish_mesh_step(const SlotDev& sd, unsigned lon
         *sd.cur ^= 1;
     }
     for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.m.smax[i] = 0ull;
+    if (sd.m.sub)
+        for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.m.sub[i] = 0ull;
     if (sd.smax2)
         for (int i = threadIdx.x; i < sd.nblk; i += blockDim.x) sd.smax2[i] = 0ull;
 }
@@ -135,8 +161,9 @@ persistent_kernel(const SlotDev* __restrict__ slots, const Item* __restrict__ it
         const SlotDev& sd = slots[w.slot];
         const int cur = __ldcg(sd.cur);
         const int z0 = w.zr ? (w.zr & 0xFFFF) : 0, z1 = w.zr ? (w.zr >> 16) : -1;
-        hydro_tile<NDIM, TX, TY, T, true, RK, FX>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX, (w.tile / sd.tiles_x) * TY,
-                                              sd.state[cur], sd.state[cur ^ 1], smem_raw, red, z0, z1, stage);
+        hydro_tile<NDIM, TX, TY, T, true, RK, FX, FilterIO>(sd.m, w.blk, (w.tile % sd.tiles_x) * TX,
+                                                        (w.tile / sd.tiles_x) * TY, sd.state[cur], sd.state[cur ^ 1],
+                                                        smem_raw, red, z0, z1, stage);
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned d = atomicAdd(sd.done, 1u);

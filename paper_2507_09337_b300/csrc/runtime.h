@@ -58,6 +58,7 @@ struct orcha_batch {
         double* scratch = nullptr;                   // fused variants: per-CTA intermediate state
         long long per_cta = 0;                       // its doubles per CTA
         unsigned long long* smax2 = nullptr;         // two-step variants: intermediate state's block speeds
+        unsigned long long* sub = nullptr;           // one-step variants: skipped cells' speed bounds per block
     } lists[orcha::kNumPrec];                        // indexed by orcha::Prec
     unsigned* queue = nullptr;
     int* cur_dev = nullptr;
