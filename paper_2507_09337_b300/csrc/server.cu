@@ -101,6 +101,7 @@ struct Req {
     double* state[2] = {nullptr, nullptr};
     double* dt = nullptr;
     unsigned long long* smax = nullptr;
+    unsigned long long* sub = nullptr;   // the signal-speed filter's per-block bounds (hydro.cuh, SpeedBound)
     int* cur = nullptr;
     unsigned* done = nullptr;
     int* err = nullptr;
@@ -218,7 +219,8 @@ bool orcha_server::admit(Req* r) {
     r->state[1] = (double*)(p + sb);
     char* tail = p + 2 * sb;
     r->smax = (unsigned long long*)tail;
-    r->dt = (double*)(tail + round_up(r->nblk * sizeof(unsigned long long)));
+    r->sub = (unsigned long long*)(tail + round_up(r->nblk * sizeof(unsigned long long)));
+    r->dt = (double*)(tail + 2 * round_up(r->nblk * sizeof(unsigned long long)));
     r->cur = (int*)((char*)r->dt + kAlign);
     r->done = (unsigned*)((char*)r->cur + kAlign);
     r->err = (int*)((char*)r->done + kAlign);
@@ -227,6 +229,7 @@ bool orcha_server::admit(Req* r) {
     const size_t tail_bytes = (size_t)((char*)r->totals + kAlign - tail);
     r->m.dt = r->dt;
     r->m.smax = r->smax;
+    r->m.sub = r->sub;
     r->m.err = r->err;
     r->err_slot = err_free.back();
     err_free.pop_back();
@@ -531,7 +534,7 @@ orcha_status orcha_server_submit(orcha_server* s, const orcha_request_desc* rd, 
     r->ncell = (long long)rd->bs[0] * rd->bs[1] * (rd->ndim == 3 ? rd->bs[2] : 1);
     r->interior_bytes = (size_t)r->nblk * r->m.nvar * r->ncell * sizeof(double);
     r->state_elems = orcha_state_elems(&md);
-    r->bytes = 2 * round_up(r->state_elems * sizeof(double)) + round_up(r->nblk * sizeof(unsigned long long)) +
+    r->bytes = 2 * round_up(r->state_elems * sizeof(double)) + 2 * round_up(r->nblk * sizeof(unsigned long long)) +
                5 * kAlign + round_up(r->nblk * 5 * sizeof(double));
     r->steps_left = rd->nsteps;
     r->kind = tile_kind(rd->ndim, r->prec, rd->bs);
