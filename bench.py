@@ -9,13 +9,17 @@ packet (halo gather, hydro task, fused dt reduction), and unpack the result.
 Metric: zone-updates/s (interior cells x time steps / s). The line also
 carries the serving latency (p50/p99 per request) of a Poisson request
 stream through the continuous-batching server and through plain
-per-request launches.
+per-request launches; for the FP64 workloads, the same workload's rate in
+the task's other arithmetics ('variants': double-word flux, which is held to
+the FP64 parity rule, and the two FP32-flux forms) and, beside the CPU
+baseline, every cell's parity against the oracle's state after the same
+number of steps for the FP64 and double-word tasks ('parity').
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload sedov256_uneven|sedov128|sedov128_f32|sedov128_f32x|sedov128_ff|sedov256_uneven_ff|
                      sedov128_rk2|sedov128_rk2_f32|sedov128_rk2_ff|sedov128_tb2|sedov128_tb2_f32|
                      sedov128_rk2_fused|sedov128_rk2_fused_f32|sedov128_amr]
-                    [--no-cpu-baseline] [--no-serving] [--serve-requests N]
+                    [--no-cpu-baseline] [--no-serving] [--no-variants] [--serve-requests N]
 
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica
 of the workload (the path has no exchange step between replicas); `value` is
@@ -110,6 +114,8 @@ def parse():
                     help="column tile of the hydro kernel (default: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other arithmetics of the FP64 workload (reported under 'variants')")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rates", default="1000,50000",
                     help="arrival rates (requests/s) of the serving leg: one below and one above saturation")
@@ -239,9 +245,29 @@ def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
 
 # ---------------------------------------------------------------- the oracle on the host cores
 
+def parity_error(G, O, nvar: int) -> float:
+    """Largest per-cell difference |g - o| / max(|o|, s_v) over cells and
+    variables, s_v the largest |momentum| for the momenta (a plain relative
+    error is meaningless where momentum vanishes by symmetry); the FP64 path's
+    tolerance is 1e-12."""
+    import numpy as np
+    mom = float(np.abs(O[:, 1:nvar - 1]).max())
+    err = 0.0
+    for v in range(nvar):
+        scale = np.abs(O[:, v])
+        if 0 < v < nvar - 1:
+            scale = np.maximum(scale, mom)
+        d = np.abs(G[:, v] - O[:, v])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.where(d == 0, 0.0, d / scale)
+        err = max(err, float(np.nanmax(r)))
+    return err
+
+
 def oracle_rate(spec, U0, seconds: float, max_steps: int = 400):
     """Zone-updates/s of the oracle on the full mesh, stepping until `seconds`
-    of wall time have passed (at least one step)."""
+    of wall time have passed (at least one step); also returns the state it
+    reached."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
@@ -255,7 +281,7 @@ def oracle_rate(spec, U0, seconds: float, max_steps: int = 400):
         el = time.perf_counter() - t0
         if el >= seconds or n >= max_steps:
             break
-    return spec.zones * n / el, threads, n, el
+    return spec.zones * n / el, threads, n, el, U
 
 
 # ---------------------------------------------------------------- reference arm
@@ -294,6 +320,63 @@ def run_reference(args):
     }
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------- other arithmetics on the same workload
+
+VARIANTS = ("ff", "f32flux", "f32flux_ffsum")
+
+
+def run_variants(B, mesh, spec, nt, U0_dev, stream, steps, dev):
+    """The same workload, device-resident and timed the same way, in the other
+    arithmetics of the hydro task: double-word flux (held to the FP64 parity
+    rule), FP32 flux in the configured arithmetic, and the FP32-flux shortcut."""
+    import torch
+    out = {}
+    h = mesh.handle
+    for name in VARIANTS:
+        task = B.TASKS[name]
+        tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
+        bt = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
+
+        def one():
+            B.orcha_mesh_load(h, U0_dev.data_ptr(), False, stream)
+            B.orcha_batch_advance(bt, task, 0, True, False, stream)
+            for _ in range(nt):
+                B.orcha_batch_advance(bt, task, 1, False, False, stream)
+
+        with torch.cuda.stream(stream):
+            one()                                   # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                one()
+            e1.record(stream)
+        stream.synchronize()
+        assert mesh.poll(stream) == 0
+        B.orcha_batch_destroy(bt)
+        out[name] = {"value": spec.zones * nt * steps / (e0.elapsed_time(e1) * 1e-3), "unit": "zone-updates/s",
+                     "dtype": DTYPES[name], "tile": f"{tile[0]}x{tile[1]}"}
+    return out
+
+
+def gpu_state_after(B, mesh, spec, task_name, U0_dev, stream, nsteps):
+    """The state after nsteps of task_name from the initial state (CFL dt from
+    it), through the persistent path, copied to the host."""
+    import torch
+    task = B.TASKS[task_name]
+    tile = B.orcha_autotune(spec.ndim, spec.bs, task, nblocks=spec.nblocks)
+    bt = B.orcha_batch_create(mesh.packets, tile[0], tile[1])
+    out = torch.empty_like(U0_dev)
+    with torch.cuda.stream(stream):
+        B.orcha_mesh_load(mesh.handle, U0_dev.data_ptr(), False, stream)
+        B.orcha_batch_advance(bt, task, nsteps, True, False, stream)
+        B.orcha_mesh_store(mesh.handle, out.data_ptr(), False, stream)
+    stream.synchronize()
+    assert mesh.poll(stream) == 0
+    B.orcha_batch_destroy(bt)
+    return out.cpu().numpy()
 
 
 # ---------------------------------------------------------------- serving latency
@@ -677,10 +760,20 @@ def main():
     }
     if not args.no_serving:
         line["latency"] = serving_latency(args)
+    if task_name == "fp64" and world == 1 and not args.no_variants:
+        line["variants"] = run_variants(B, mesh, spec, nt, U0_dev, stream, args.steps, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, n, el = oracle_rate(spec, U0_host, args.cpu_seconds)
+        rate, cores, n, el, U_oracle = oracle_rate(spec, U0_host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{n} time steps of the full {spec.zones}-zone mesh in {el:.1f} s"}
+        if task_name == "fp64":
+            # parity at the full size: every cell after the oracle's n steps,
+            # against the FP64 task and the double-word one (rule: 1e-12)
+            line["parity"] = {"steps": n, "rule": "max over cells |g - o| / max(|o|, largest |momentum| for momenta)",
+                              "tolerance": 1e-12}
+            for name in ("fp64", "ff"):
+                G = gpu_state_after(B, mesh, spec, name, U0_dev, stream, n)
+                line["parity"][name] = parity_error(G, U_oracle, spec.nvar)
     B.orcha_batch_destroy(batch)
     for mk, bk in extra:
         B.orcha_batch_destroy(bk)
