@@ -174,8 +174,8 @@ __device__ __forceinline__ float d2f_rn(double x) {
     return __uint_as_float(sign | r);
 }
 
-// binary32 -> binary64 (exact).
-__device__ __forceinline__ double f2d(float x) {
+// binary32 -> binary64 (exact), every case.
+__device__ __forceinline__ double f2d_any(float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned a = b & 0x7FFFFFFFu;
     const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
@@ -192,6 +192,21 @@ __device__ __forceinline__ double f2d(float x) {
         r = ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)a << (52 - p)) & 0xFFFFFFFFFFFFFull);
     }
     return __longlong_as_double((long long)(sign | r));
+}
+
+// binary32 -> binary64 (exact): normal numbers and zeros in a few integer
+// instructions -- the high word is the sign, the exponent rebiased by
+// 1023 - 127 = 896 and the top 20 fraction bits, the low word the last 3
+// fraction bits -- and the rare subnormals, infinities and NaNs by the
+// general form behind a branch.
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned a = b & 0x7FFFFFFFu;
+    if (a - 0x00800000u < 0x7F000000u || a == 0u) {
+        const unsigned hi = (b & 0x80000000u) | (a ? (a >> 3) + (896u << 20) : 0u);
+        return __hiloint2double((int)hi, (int)(a << 29));
+    }
+    return f2d_any(x);
 }
 
 // Which conversions the FP32-flux path issues, per direction: the
