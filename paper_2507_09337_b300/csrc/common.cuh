@@ -144,8 +144,8 @@ template <> struct P<rd> {
 // conversions (NaN payloads aside); checked on the GPU by
 // orcha_selftest_conversions.
 
-// binary64 -> binary32, round to nearest, ties to even.
-__device__ __forceinline__ float d2f_rn(double x) {
+// binary64 -> binary32, round to nearest, ties to even; every case.
+__device__ __forceinline__ float d2f_any(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -194,6 +194,26 @@ __device__ __forceinline__ double f2d_any(float x) {
     return __longlong_as_double((long long)(sign | r));
 }
 
+// binary64 -> binary32, round to nearest, ties to even: a normal binary32
+// result (or an overflow by rounding) in a few integer instructions -- the
+// top 23 fraction bits and the exponent rebiased by 896 (its 9 low bits plus
+// 128, mod 512, for biased exponents 897 .. 1150), plus one unit where the 29
+// dropped bits exceed half a unit or equal it with an odd result -- zeros
+// directly, and the rest (subnormal results, overflow, infinities, NaN) by
+// the general form behind a branch.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+    const unsigned a = hi & 0x7FFFFFFFu;
+    if ((a >> 20) - 897u <= 253u) {
+        unsigned r = __funnelshift_l(lo, a, 3) + 0x40000000u;
+        const unsigned rem = lo & 0x1FFFFFFFu;
+        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float(r | (hi & 0x80000000u));
+    }
+    if ((a | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return d2f_any(x);
+}
+
 // binary32 -> binary64 (exact): normal numbers and zeros in a few integer
 // instructions -- the high word is the sign, the exponent rebiased by
 // 1023 - 127 = 896 and the top 20 fraction bits, the low word the last 3
@@ -213,7 +233,10 @@ __device__ __forceinline__ double f2d(float x) {
 // integer-pipe forms above (1) or the hardware conversions (0). All are
 // exact, so results do not depend on the choice; it balances FP64-pipe
 // slots (one per hardware conversion) against integer instructions (about
-// 15 per narrowing, 6 per widening). Measured on a B300 (FP32-flux bench).
+// 8 per narrowing and 5 per widening on their fast paths). Measured on a
+// B300 (C2 set-up): widening on the integer pipe is faster (the FP64 pipe
+// carries the configured arithmetic's update), narrowing there is slower
+// (FP32 flux 6.61 against 6.72 G, the shortcut 7.6 against 9.1 G).
 #ifndef ORCHA_D2F_ON_INT_PIPE
 #define ORCHA_D2F_ON_INT_PIPE 0
 #endif
