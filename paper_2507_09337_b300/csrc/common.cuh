@@ -123,6 +123,11 @@ template <> struct P<rd> {
     // subnormal range and is the magnitude bits shifted right by one with the
     // dropped bit rounded to nearest even (the IEEE result bit for bit).
     static __device__ __forceinline__ rd half(rd x) {
+        // the common case (a normal result): one decrement of the exponent
+        // field in the high word
+        const unsigned hi = (unsigned)__double2hiint(x.v);
+        if (((hi >> 20) & 0x7FFu) - 2u <= 0x7FCu)
+            return rd(__hiloint2double((int)(hi - 0x00100000u), __double2loint(x.v)));
         const unsigned long long b = (unsigned long long)bits(x);
         const unsigned long long sign = b & 0x8000000000000000ull, a = b & 0x7FFFFFFFFFFFFFFFull;
         const unsigned e = (unsigned)(a >> 52);
