@@ -74,11 +74,6 @@ template <class T> struct P;
 // integer forms below give bitwise the same answers (NaN never reaches them
 // on a physical state; the non-physical checks run on finite values).
 __device__ __forceinline__ long long bits(rd x) { return __double_as_longlong(x.v); }
-// Totally ordered integer key of a non-NaN double; -0 and +0 share key 0.
-__device__ __forceinline__ long long okey(rd x) {
-    const long long b = bits(x);
-    return b < 0 ? -(b & 0x7FFFFFFFFFFFFFFFLL) : b;
-}
 
 template <> struct P<rd> {
     using store = double;
@@ -106,9 +101,26 @@ template <> struct P<rd> {
         const unsigned long long b = (unsigned long long)bits(x);
         return b > 0x8000000000000000ULL && b <= 0xFFF0000000000000ULL;
     }
-    static __device__ __forceinline__ bool lt(rd a, rd b) { return okey(a) < okey(b); }
-    static __device__ __forceinline__ bool ge0(rd a) { return okey(a) >= 0; }
-    static __device__ __forceinline__ bool le0(rd a) { return okey(a) <= 0; }
+    // a < b for non-NaN values, except that -0 < +0 here (the bit pattern
+    // with the magnitude bits of a negative number flipped is a signed
+    // integer key in value order): the HLL wave speeds, its only use, can
+    // then differ from those of a value comparison at most in the sign of a
+    // zero, which ge0 and le0 do not see, so every flux has the same bits.
+    static __device__ __forceinline__ bool lt(rd a, rd b) {
+        const long long ba = bits(a), bb = bits(b);
+        return (ba ^ (long long)((unsigned long long)(ba >> 63) >> 1)) <
+               (bb ^ (long long)((unsigned long long)(bb >> 63) >> 1));
+    }
+    // a >= 0 and a <= 0 with -0 == +0 (sign clear or -0; sign set or +0),
+    // from the high word
+    static __device__ __forceinline__ bool ge0(rd a) {
+        const unsigned hi = (unsigned)__double2hiint(a.v);
+        return (int)hi >= 0 || ((hi & 0x7FFFFFFFu) | (unsigned)__double2loint(a.v)) == 0u;
+    }
+    static __device__ __forceinline__ bool le0(rd a) {
+        const unsigned hi = (unsigned)__double2hiint(a.v);
+        return (int)hi < 0 || (hi | (unsigned)__double2loint(a.v)) == 0u;
+    }
     // minmod: same strict sign -> the argument of smaller magnitude, else +0
     static __device__ __forceinline__ rd minmod(rd a, rd b) {
         const long long ba = bits(a), bb = bits(b);
