@@ -819,27 +819,50 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
         }
         return ok;
     };
-    // Owner cells: every face state Wb -+ dW/2 (flo / fhi), or Wc on fallback.
-    auto predict = [&](int pzi, int c2, T (&flo)[3][NV], T (&fhi)[3][NV]) {
+    // Owner cells: every face state Wb -+ dW/2, or Wc on fallback. The x and
+    // y face states of an inner plane go to shared memory as soon as they
+    // are formed, beside the positivity test, and a cell that falls back
+    // (rare) overwrites them with Wc: the same values end up in the same
+    // places as with the test first, without the stores waiting for it.
+    // The z face states stay in registers (zlo, zhi).
+    auto predict_owner = [&](int pzi, bool inner, T (&zlo)[NV], T (&zhi)[NV]) {
         A2 Wc[NV], dW[3][NV], Wb[NV];
-        predict_core(pzi, c2, Wc, dW, Wb);
+        predict_core(pzi, o2, Wc, dW, Wb);
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
+            T lo[NV], hi[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const A2 hs = P<A2>::half(dW[d][v]);
-                flo[d][v] = as<T>(Wb[v] - hs);
-                fhi[d][v] = as<T>(Wb[v] + hs);
+                lo[v] = as<T>(Wb[v] - hs);
+                hi[v] = as<T>(Wb[v] + hs);
             }
-            ok = ok && P<T>::pos(flo[d][0]) && P<T>::pos(flo[d][NV - 1]) && P<T>::pos(fhi[d][0]) &&
-                 P<T>::pos(fhi[d][NV - 1]);
+            ok = ok && P<T>::pos(lo[0]) && P<T>::pos(lo[NV - 1]) && P<T>::pos(hi[0]) && P<T>::pos(hi[NV - 1]);
+            if (d < 2) {
+                if (inner) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        P<T>::st(&sFS[((2 * d) * NV + v) * R1N + o1], lo[v]);
+                        P<T>::st(&sFS[((2 * d + 1) * NV + v) * R1N + o1], hi[v]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { zlo[v] = lo[v]; zhi[v] = hi[v]; }
+            }
         }
         if (!ok) {
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d)
+            for (int v = 0; v < NV; ++v) {
+                const T w = as<T>(Wc[v]);
+                if (inner) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) { flo[d][v] = as<T>(Wc[v]); fhi[d][v] = as<T>(Wc[v]); }
+                    for (int f = 0; f < 4; ++f) P<T>::st(&sFS[(f * NV + v) * R1N + o1], w);
+                }
+                zlo[v] = w;
+                zhi[v] = w;
+            }
         }
     };
     // Ring cells: only the one x or y face state the tile needs (face 0..3 =
@@ -959,23 +982,7 @@ __device__ __forceinline__ void hydro_tile(const MeshDev& m, const int blk, cons
 
         // ---- P: predict
         T zlo[NV], zhi[NV];
-        if (owner) {
-            T flo[3][NV], fhi[3][NV];
-            predict(p, o2, flo, fhi);
-            if (inner) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    P<T>::st(&sFS[(0 * NV + v) * R1N + o1], flo[0][v]);
-                    P<T>::st(&sFS[(1 * NV + v) * R1N + o1], fhi[0][v]);
-                    P<T>::st(&sFS[(2 * NV + v) * R1N + o1], flo[1][v]);
-                    P<T>::st(&sFS[(3 * NV + v) * R1N + o1], fhi[1][v]);
-                }
-            }
-            if (NDIM == 3) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) { zlo[v] = flo[2][v]; zhi[v] = fhi[2][v]; }
-            }
-        }
+        if (owner) predict_owner(p, inner, zlo, zhi);
         // ring cells: the one face state the tile reads, the same bits as the
         // owner of that cell forms (the FP64 operations and their fusion are
         // fixed by the source, so both evaluations agree)
