@@ -502,7 +502,12 @@ ORCHA_API orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64
  * This checks them against the hardware instructions on `count`
  * pseudo-random operand pairs derived from `seed` (biased toward carries,
  * ties, cancellation and zeros); *mismatches receives the number of results
- * whose bits differ (NaN results excepted). Synchronous. */
+ * whose bits differ (NaN results excepted). The same pairs also check the
+ * FP64 task's integer-pipe sign tests (x > 0, x < 0, x >= 0, x <= 0), the
+ * order of its HLL wave speeds (x < y, except that -0 counts below +0),
+ * minmod and the halving 0.5 * x against FP64 comparisons and the hardware
+ * multiply (NaN operands excepted), each disagreement counted as a mismatch.
+ * Synchronous. */
 ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64_t* mismatches);
 
 /* Diagnostics: the FF task computes in double-word arithmetic (pairs of

@@ -317,7 +317,9 @@ __global__ void selftest_kernel(unsigned long long lo, unsigned long long n, uns
 // pairs: half unrelated (any exponent, mantissas near all-ones or near zero,
 // exact zeros), half related (the second is the first with a flipped sign,
 // low mantissa bits perturbed and the exponent moved by a few), which
-// exercises carries, ties and cancellation.
+// exercises carries, ties and cancellation. The same pairs check the FP64
+// task's integer forms of the sign tests, the wave-speed order, minmod and
+// the halving against FP64 comparisons and 0.5 * x.
 __device__ __forceinline__ unsigned long long rand_double_bits(unsigned long long z) {
     const unsigned long long r = mix64(z), r2 = mix64(z ^ 0x5DEECE66Dull);
     const unsigned k = (unsigned)(r2 % 6);
@@ -353,6 +355,20 @@ __global__ void selftest_fp64_kernel(unsigned long long n, unsigned long long se
         cnt += (__double_as_longlong(m1) != __double_as_longlong(m2)) && !(m2 != m2);
         cnt += (__double_as_longlong(a1) != __double_as_longlong(a2)) && !(a2 != a2);
         cnt += (__double_as_longlong(s1) != __double_as_longlong(s2)) && !(s2 != s2);
+        // the FP64 task's integer-pipe sign tests, selects and halving against
+        // FP64 comparisons and multiplication (NaN operands excepted)
+        if (!(x != x) && !(y != y)) {
+            const rd X(x), Y(y);
+            const bool zz = x == 0.0 && y == 0.0 && signbit(x) && !signbit(y);   // -0 < +0 in lt only
+            cnt += P<rd>::lt(X, Y) != ((x < y) || zz);
+            cnt += P<rd>::ge0(X) != (x >= 0.0);
+            cnt += P<rd>::le0(X) != (x <= 0.0);
+            cnt += P<rd>::pos(X) != (x > 0.0);
+            cnt += P<rd>::neg(X) != (x < 0.0);
+            const double mm = (x > 0.0 && y > 0.0) ? (x < y ? x : y) : ((x < 0.0 && y < 0.0) ? (x > y ? x : y) : 0.0);
+            cnt += __double_as_longlong(P<rd>::minmod(X, Y).v) != __double_as_longlong(mm);
+            cnt += __double_as_longlong(P<rd>::half(X).v) != __double_as_longlong(__dmul_rn(0.5, x));
+        }
     }
     if (cnt) atomicAdd(bad, cnt);
 }

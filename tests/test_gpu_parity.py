@@ -214,7 +214,9 @@ def test_c4_f32flux_100_steps_error_against_fp64_oracle(oracle_mod, task):
 
 def test_integer_pipe_fp64_arithmetic_matches_hardware():
     """The integer-pipe binary64 add/sub/mul give the hardware's bits on 2^31
-    pseudo-random operand pairs (carries, ties, cancellation, zeros)."""
+    pseudo-random operand pairs (carries, ties, cancellation, zeros), and the
+    FP64 task's integer sign tests, wave-speed order, minmod and halving
+    agree with FP64 comparisons and 0.5 * x on the same pairs."""
     assert B.orcha_selftest_fp64_emulation(1 << 31, seed=2024) == 0
 
 
