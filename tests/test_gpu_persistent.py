@@ -34,18 +34,36 @@ def test_sedov128_batch_matches_packet_path_and_oracle(oracle_mod):
     assert rule12_error(G, O, spec.nvar) <= TOL
 
 
-def test_sedov256_uneven_packets_two_steps(oracle_mod):
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_FF])
+def test_sedov256_uneven_packets_two_steps(oracle_mod, task):
     """256^3 cells as 4096 blocks of 16^3, packet sizes seed-uniform in
-    [1, 256]: every cell after two steps (graph-captured)."""
+    [1, 256]: every cell after two steps (graph-captured), in FP64 and in the
+    double-word arithmetic, both held to the FP64 rule."""
     spec, packets = wl.sedov256_uneven_packets(0)
     assert min(len(p) for p in packets) >= 1 and sum(len(p) for p in packets) == 4096
     U0 = wl.sedov_state(spec)
-    (G,), errs = gpu_batch_steps([(spec, U0, packets)], 2, use_graph=True)
+    (G,), errs = gpu_batch_steps([(spec, U0, packets)], 2, task=task, use_graph=True)
     assert errs == [0]
     O, _ = oracle_steps(oracle_mod, spec, U0, 2)
     e = rule12_error(G, O, spec.nvar)
-    print(f"sedov256 uneven packets, 2 steps: rule-12 error {e:.3e}")
+    print(f"sedov256 uneven packets, 2 steps, task {task}: rule-12 error {e:.3e}")
     assert e <= TOL
+
+
+def test_sedov256_f32flux_error_and_conservation(oracle_mod):
+    """The same 256^3 mesh in the configured FP32-flux arithmetic: L1(rho)
+    against the FP64 oracle after two steps, stated; mass and energy totals
+    conserved to 1e-13 (the blast stays inside)."""
+    spec, packets = wl.sedov256_uneven_packets(0)
+    U0 = wl.sedov_state(spec)
+    (G,), errs = gpu_batch_steps([(spec, U0, packets)], 2, task=B.ORCHA_TASK_HYDRO_F32FLUX, use_graph=True)
+    assert errs == [0]
+    O, _ = oracle_steps(oracle_mod, spec, U0, 2)
+    l1 = float(np.abs(G[:, 0] - O[:, 0]).mean()) / float(np.abs(O[:, 0]).mean())
+    print(f"sedov256 FP32 flux, 2 steps: relative L1(rho) {l1:.3e}")
+    assert l1 < 1e-6
+    for v in (0, 4):
+        assert abs(G[:, v].sum() - U0[:, v].sum()) <= 1e-13 * abs(U0[:, v].sum())
 
 
 @pytest.mark.parametrize("tile", [(8, 8), (16, 8), (16, 16)])
