@@ -334,10 +334,11 @@ template <> struct P<float> {
     static __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
     static __device__ __forceinline__ bool ge0(float a) { return a >= 0.0f; }
     static __device__ __forceinline__ bool le0(float a) { return a <= 0.0f; }
+    // without branches: the smaller magnitude with a's sign when both have
+    // one strict sign (sign bits equal, neither zero), else +0
     static __device__ __forceinline__ float minmod(float a, float b) {
-        if (a > 0.0f && b > 0.0f) return (a < b) ? a : b;
-        if (a < 0.0f && b < 0.0f) return (a > b) ? a : b;
-        return 0.0f;
+        const bool ok = ((__float_as_int(a) ^ __float_as_int(b)) >= 0) & (a != 0.0f) & (b != 0.0f);
+        return ok ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
     }
     static __device__ __forceinline__ float half(float x) { return 0.5f * x; }
     static __device__ __forceinline__ float zero() { return 0.0f; }
