@@ -374,10 +374,13 @@ template <> struct P<dw> {
     static __device__ __forceinline__ bool lt(dw a, dw b) { return dw_lt(a, b); }
     static __device__ __forceinline__ bool ge0(dw a) { return a.hi >= 0.0f; }
     static __device__ __forceinline__ bool le0(dw a) { return a.hi <= 0.0f; }
+    // without branches: both positive -> the smaller, both negative -> the
+    // larger, else 0
     static __device__ __forceinline__ dw minmod(dw a, dw b) {
-        if (a.hi > 0.0f && b.hi > 0.0f) return dw_lt(a, b) ? a : b;
-        if (a.hi < 0.0f && b.hi < 0.0f) return dw_lt(b, a) ? a : b;
-        return dw{0.0f, 0.0f};
+        const bool pos = (a.hi > 0.0f) & (b.hi > 0.0f), neg = (a.hi < 0.0f) & (b.hi < 0.0f);
+        const bool take_a = pos ? dw_lt(a, b) : dw_lt(b, a);
+        const dw m = take_a ? a : b;
+        return (pos | neg) ? m : dw{0.0f, 0.0f};
     }
     static __device__ __forceinline__ dw half(dw x) { return {__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)}; }
     static __device__ __forceinline__ dw zero() { return dw{0.0f, 0.0f}; }

@@ -106,6 +106,6 @@ __device__ __forceinline__ dw dw_rsqrt(dw y) {
 }
 
 // Totally ordered comparison of normalised double-words.
-__device__ __forceinline__ bool dw_lt(dw a, dw b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool dw_lt(dw a, dw b) { return (a.hi < b.hi) | ((a.hi == b.hi) & (a.lo < b.lo)); }
 
 }  // namespace orcha
