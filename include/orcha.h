@@ -506,7 +506,9 @@ ORCHA_API orcha_status orcha_selftest_conversions(uint64_t first_pattern, uint64
  * FP64 task's integer-pipe sign tests (x > 0, x < 0, x >= 0, x <= 0), the
  * order of its HLL wave speeds (x < y, except that -0 counts below +0),
  * minmod and the halving 0.5 * x against FP64 comparisons and the hardware
- * multiply (NaN operands excepted), each disagreement counted as a mismatch.
+ * multiply (NaN operands excepted), and the FP32 tasks' minmod (a median of
+ * three) against its sign-test definition on binary32 pairs cut from the
+ * same operands, bit for bit; each disagreement counted as a mismatch.
  * Synchronous. */
 ORCHA_API orcha_status orcha_selftest_fp64_emulation(uint64_t count, uint64_t seed, uint64_t* mismatches);
 

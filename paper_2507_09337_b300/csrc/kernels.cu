@@ -319,7 +319,8 @@ __global__ void selftest_kernel(unsigned long long lo, unsigned long long n, uns
 // low mantissa bits perturbed and the exponent moved by a few), which
 // exercises carries, ties and cancellation. The same pairs check the FP64
 // task's integer forms of the sign tests, the wave-speed order, minmod and
-// the halving against FP64 comparisons and 0.5 * x.
+// the halving against FP64 comparisons and 0.5 * x, and the FP32 tasks'
+// minmod against FP32 comparisons.
 __device__ __forceinline__ unsigned long long rand_double_bits(unsigned long long z) {
     const unsigned long long r = mix64(z), r2 = mix64(z ^ 0x5DEECE66Dull);
     const unsigned k = (unsigned)(r2 % 6);
@@ -368,6 +369,20 @@ __global__ void selftest_fp64_kernel(unsigned long long n, unsigned long long se
             const double mm = (x > 0.0 && y > 0.0) ? (x < y ? x : y) : ((x < 0.0 && y < 0.0) ? (x > y ? x : y) : 0.0);
             cnt += __double_as_longlong(P<rd>::minmod(X, Y).v) != __double_as_longlong(mm);
             cnt += __double_as_longlong(P<rd>::half(X).v) != __double_as_longlong(__dmul_rn(0.5, x));
+        }
+        // the FP32 minmod (FP32-flux tasks) against its sign-test definition,
+        // both argument orders, on binary32 pairs taken from the high and the
+        // low words of the operands (zeros of both signs, ties, subnormals,
+        // infinities; NaN excepted)
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const float fx = __uint_as_float((unsigned)(w ? a : a >> 32)), fy = __uint_as_float((unsigned)(w ? b : b >> 32));
+            if (!(fx != fx) && !(fy != fy)) {
+                const float fm = (fx > 0.0f && fy > 0.0f) ? (fx < fy ? fx : fy)
+                                                          : ((fx < 0.0f && fy < 0.0f) ? (fx > fy ? fx : fy) : 0.0f);
+                cnt += __float_as_uint(P<float>::minmod(fx, fy)) != __float_as_uint(fm);
+                cnt += __float_as_uint(P<float>::minmod(fy, fx)) != __float_as_uint(fm);
+            }
         }
     }
     if (cnt) atomicAdd(bad, cnt);

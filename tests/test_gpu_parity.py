@@ -216,7 +216,9 @@ def test_integer_pipe_fp64_arithmetic_matches_hardware():
     """The integer-pipe binary64 add/sub/mul give the hardware's bits on 2^31
     pseudo-random operand pairs (carries, ties, cancellation, zeros), and the
     FP64 task's integer sign tests, wave-speed order, minmod and halving
-    agree with FP64 comparisons and 0.5 * x on the same pairs."""
+    agree with FP64 comparisons and 0.5 * x on the same pairs; the FP32
+    tasks' median-of-three minmod gives the bits of its sign-test definition
+    on binary32 pairs cut from them (zeros of both signs, ties)."""
     assert B.orcha_selftest_fp64_emulation(1 << 31, seed=2024) == 0
 
 
