@@ -530,7 +530,9 @@ ORCHA_API orcha_status orcha_selftest_dword(uint64_t count, uint64_t seed, doubl
  * bound against the FP64 speed on `count` pseudo-random 3D states derived
  * from `seed` (densities 2^-20 .. 2^20, speeds up to 10^6, pressures down to
  * 10^-14 of the kinetic energy density): counts[0] = states where the bound
- * applied but lies below the FP64 speed (0 when the bound is sound),
+ * applied but lies below the FP64 speed, or where the lower bound that the
+ * first time step's filter pairs with it (the same conditions, the same upper
+ * bits) lies above the FP64 speed (0 when both are sound),
  * counts[1] = states where it applied, counts[2] = states where it applied
  * although the FP64 evaluation finds the state non-physical (0 when sound);
  * *max_ratio = the largest bound / speed ratio. Synchronous. Errors:

@@ -597,8 +597,9 @@ static orcha_status ensure_list(orcha_batch* b, int prec) {
         // one-step variants: the signal-speed filter's per-block bounds (hydro.cuh, SpeedBound)
         long long nb_all = 0;
         for (auto* m : b->meshes) nb_all += m->nblk;
-        e = cudaMalloc(&L.sub, sizeof(unsigned long long) * (size_t)nb_all);
-        if (e == cudaSuccess) e = cudaMemset(L.sub, 0, sizeof(unsigned long long) * (size_t)nb_all);
+        // + one word per mesh: the first dt's scratch (orcha::launch_first_dt)
+        e = cudaMalloc(&L.sub, sizeof(unsigned long long) * (size_t)(nb_all + (long long)ns));
+        if (e == cudaSuccess) e = cudaMemset(L.sub, 0, sizeof(unsigned long long) * (size_t)(nb_all + (long long)ns));
         long long off = 0;
         for (size_t i = 0; i < ns; ++i) {
             sl[i].m.sub = L.sub + off;
@@ -660,12 +661,27 @@ orcha_status orcha_batch_advance(orcha_batch* b, orcha_task task, int32_t nsteps
     orcha_status s;
     if ((s = ensure_list(b, orcha::prec_of(task)))) return s;
     if (init_dt) {
-        // one launch per mesh over all its blocks (the batch covers every block)
-        for (auto* m : b->meshes) {
-            ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st,
-                                                      orcha::prec_f32_dt(orcha::prec_of(task))),
-                       "batch signal speed");
-            if ((s = orcha_dt_reduce(m, stream))) return s;
+        // one launch per mesh over all its blocks (the batch covers every block);
+        // an FP64 rule with the list's filter bounds takes the filtered first dt
+        const orcha_batch::List& L = b->lists[orcha::prec_of(task)];
+        long long nb_all = 0;
+        for (auto* m : b->meshes) nb_all += m->nblk;
+        long long off = 0;
+        for (size_t i = 0; i < b->meshes.size(); ++i) {
+            orcha_mesh* m = b->meshes[i];
+            if (L.sub && !orcha::prec_f32_dt(orcha::prec_of(task))) {
+                orcha::MeshDev md = m->dev;
+                md.sub = L.sub + off;
+                ORCHA_CUDA(orcha::launch_first_dt(md, m->nblk, m->desc.state_dev[m->cur], m->desc.dt_dev,
+                                                  L.sub + nb_all + (long long)i, st),
+                           "batch first dt");
+            } else {
+                ORCHA_CUDA(orcha::launch_signal_speed_all(m->dev, m->nblk, m->desc.state_dev[m->cur], st,
+                                                          orcha::prec_f32_dt(orcha::prec_of(task))),
+                           "batch signal speed");
+                if ((s = orcha_dt_reduce(m, stream))) return s;
+            }
+            off += m->nblk;
         }
     }
     // the device copy of each mesh's current buffer index, as of this point in the stream

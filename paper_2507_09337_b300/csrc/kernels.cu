@@ -119,6 +119,136 @@ __global__ void signal_speed_all_kernel(const MeshDev m, const double* __restric
     cta_raise_smax(__longlong_as_double((long long)b), red, &m.smax[blk]);     // max: any chunk order
 }
 
+// ---------------------------------------------------------------- first CFL time step, filtered
+// The first dt of a state needs the largest FP64 signal speed over all its
+// cells and has no previous maximum to filter against (hydro.cuh, signal-
+// speed filter). Pass 1 takes every cell's rigorous FP32 bounds lb <= s <= ub
+// of its FP64 speed s (speed_bounds, below), or s itself where they do not apply,
+// and raises the block's largest ub (m.sub), the exactly evaluated speeds
+// (m.smax) and the state's largest lb or exact speed (*lbmax). That is at
+// most the largest speed, so a cell with ub < *lbmax cannot hold it: pass 2
+// evaluates in FP64 only the cells with ub >= *lbmax, in the blocks whose
+// m.sub reaches it. The maximum over m.smax is then the maximum over every
+// cell, bit for bit, and the non-physical flag is raised as by the full
+// evaluation (a cell whose bounds apply has a positive FP64 pressure).
+// The lower-side constants of the bounds: gamma and 1/dx_d rounded down.
+struct SpeedBoundLo {
+    float g_lo, idx_lo[3];
+};
+__device__ __forceinline__ SpeedBoundLo speed_bound_lo_setup(const MeshDev& m) {
+    SpeedBoundLo b;
+    b.g_lo = __double2float_rd(m.gamma);
+    for (int d = 0; d < 3; ++d) b.idx_lo[d] = __double2float_rd(m.idx[d]);
+    return b;
+}
+
+// The upper bound ub of speed_upper (hydro.cuh; the same operations, so the
+// same bits) and a lower bound lb <= the FP64 signal speed of Un: the mirror
+// of the upper bound's steps, every operation rounded down (|m_d| / rho from
+// the truncated |m_d| times 1/rho rounded down, the pressure's lower bound
+// pl, sqrt(gamma pl / rho) rounded down, the sum times 1/dx_d rounded down),
+// divided by `margin`, which covers the FP64 evaluation's own rounding on
+// this side as on the other. False where the bounds do not apply (the
+// conditions of speed_upper).
+template <int NDIM>
+__device__ __forceinline__ bool speed_bounds(const SpeedBound& sb, const SpeedBoundLo& sl, const rd* Un, float& lb,
+                                             float& ub) {
+    constexpr int NV = NDIM + 2;
+    constexpr float kUp = 0x1.000002p0f;
+    float rl, el, ml[NDIM];
+    bool ok = mag_f32_rz(Un[0].v, rl) && mag_f32_rz(Un[NV - 1].v, el) && __double_as_longlong(Un[0].v) > 0 &&
+              __double_as_longlong(Un[NV - 1].v) > 0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) ok = mag_f32_rz(Un[1 + d].v, ml[d]) && ok;
+    if (!ok) return false;
+    const float rh = __fmul_ru(rl, kUp), eh = __fmul_ru(el, kUp);
+    const float ri_hi = __frcp_ru(rl), ri_lo = __frcp_rd(rh);
+    float kel = 0.0f, keh = 0.0f, ah[NDIM], al[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const float mh = __fmul_ru(ml[d], kUp);
+        ah[d] = __fmul_ru(mh, ri_hi);
+        al[d] = __fmul_rd(ml[d], ri_lo);                             // <= |m_d| / rho
+        kel = __fadd_rd(kel, __fmul_rd(ml[d], __fmul_rd(ml[d], ri_lo)));
+        keh = __fadd_ru(keh, __fmul_ru(mh, ah[d]));
+    }
+    kel = 0.5f * kel;
+    keh = 0.5f * keh;
+    const float pl = __fmul_rd(sb.gm1_lo, __fadd_rd(el, -keh));
+    if (!(pl > eh * 0x1p-40f)) return false;
+    const float ph = __fmul_ru(sb.gm1_hi, __fadd_ru(eh, -kel));
+    const float ch = __fsqrt_ru(__fmul_ru(__fmul_ru(sb.g_hi, ph), ri_hi));
+    const float cl = __fsqrt_rd(__fmul_rd(__fmul_rd(sl.g_lo, pl), ri_lo));   // <= sqrt(gamma p / rho)
+    float s = 0.0f, t = 0.0f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        s = __fadd_ru(s, __fmul_ru(__fadd_ru(ah[d], ch), sb.idx_hi[d]));
+        t = __fadd_rd(t, __fmul_rd(__fadd_rd(al[d], cl), sl.idx_lo[d]));
+    }
+    ub = __fmul_ru(s, sb.margin);
+    lb = __fdiv_rd(t, sb.margin);
+    return true;
+}
+
+template <int NDIM>
+__device__ __forceinline__ void cell_state(const MeshDev& m, const double* __restrict__ Ub, int c, rd (&Un)[NDIM + 2]) {
+    const int i = c % m.bs[0], r0 = c / m.bs[0], j = r0 % m.bs[1], k = r0 / m.bs[1];
+    const int kk = (NDIM == 3) ? k + kGuard : 0;
+    const int po = (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
+#pragma unroll
+    for (int v = 0; v < NDIM + 2; ++v) Un[v] = rd(Ub[po + v * m.var_stride]);
+}
+
+template <int NDIM>
+__global__ void first_dt_bounds_kernel(const MeshDev m, const double* __restrict__ U,
+                                       unsigned long long* __restrict__ lbmax) {
+    __shared__ unsigned long long red[32];
+    const int blk = blockIdx.x;
+    const double* Ub = U + (long long)blk * m.blk_stride;
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const SpeedBound sb = speed_bound_setup(m, 1.0);
+    const SpeedBoundLo sl = speed_bound_lo_setup(m);
+    float ubm = 0.0f, lbm = 0.0f;
+    unsigned long long em = 0ull;        // bits of the largest exactly evaluated speed
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncell; c += gridDim.y * blockDim.x) {
+        rd Un[NDIM + 2];
+        cell_state<NDIM>(m, Ub, c, Un);
+        float lb, ub;
+        if (speed_bounds<NDIM>(sb, sl, Un, lb, ub)) {
+            ubm = fmaxf(ubm, ub);
+            lbm = fmaxf(lbm, lb);
+        } else {
+            em = umax64(em, new_state_speed<rd, NDIM>(m, Un));
+        }
+    }
+    const unsigned long long ubb = (unsigned long long)__double_as_longlong((double)ubm);
+    const unsigned long long lbb = umax64((unsigned long long)__double_as_longlong((double)lbm), em);
+    cta_raise_smax2(ubb, em, red, &m.sub[blk], &m.smax[blk]);
+    __syncthreads();
+    cta_raise_smax(__longlong_as_double((long long)lbb), red, lbmax);
+}
+
+template <int NDIM>
+__global__ void first_dt_eval_kernel(const MeshDev m, const double* __restrict__ U,
+                                     const unsigned long long* __restrict__ lbmax) {
+    __shared__ unsigned long long red[32];
+    const int blk = blockIdx.x;
+    const unsigned long long L = *lbmax;
+    if (m.sub[blk] < L) return;          // the whole CTA: no cell of this block reaches L
+    const double* Ub = U + (long long)blk * m.blk_stride;
+    const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
+    const SpeedBound sb = speed_bound_setup(m, 1.0);
+    unsigned long long em = 0ull;
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncell; c += gridDim.y * blockDim.x) {
+        rd Un[NDIM + 2];
+        cell_state<NDIM>(m, Ub, c, Un);
+        float ub;      // cells without bounds were evaluated by pass 1
+        if (speed_upper<NDIM>(sb, Un, ub) && (unsigned long long)__double_as_longlong((double)ub) >= L)
+            em = umax64(em, new_state_speed<rd, NDIM>(m, Un));
+    }
+    cta_raise_smax(__longlong_as_double((long long)em), red, &m.smax[blk]);
+}
+
 // ---------------------------------------------------------------- dt reduction
 // dt = cfl / max over blocks; then clear the per-block maxima for the next step.
 __global__ void dt_reduce_kernel(const MeshDev m, int nblk, double* __restrict__ dt) {
@@ -471,16 +601,21 @@ __global__ void selftest_speed_bound_kernel(unsigned long long n, unsigned long 
         for (int d = 0; d < 3; ++d) Un[1 + d] = rd(rho * u[d]);
         Un[4] = rd(pr / m.gm1 + ke);
         SpeedBound sb = speed_bound_setup(m, 1.0);
-        float ub;
-        if (!speed_upper<3>(sb, Un, ub)) continue;
+        float ub, lb, ub2;
+        const bool two = speed_bounds<3>(sb, speed_bound_lo_setup(m), Un, lb, ub2);   // the first dt's pair
+        if (!speed_upper<3>(sb, Un, ub)) {
+            bad += two;                                         // both apply under the same conditions
+            continue;
+        }
         ++applied;
+        if (!two || __float_as_uint(ub2) != __float_as_uint(ub)) { ++bad; continue; }
         rd W[5], r;
         prim_from_cons<rd, 3>(Un, W, r, rd(m.gm1));
         if (!(P<rd>::pos(W[0]) && P<rd>::pos(W[4]))) { ++nonphys; continue; }
         m.err = err_sink;
         const double s = __longlong_as_double((long long)new_state_speed<rd, 3>(m, Un));
         const double b = (double)ub;
-        if (!(b >= s)) ++bad;
+        if (!(b >= s) || !((double)lb <= s)) ++bad;
         worst = fmax(worst, b / s);
     }
     if (bad) atomicAdd(&res[0], bad);
@@ -702,6 +837,25 @@ cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U,
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st) {
     dt_reduce_kernel<<<1, 1024, 0, st>>>(m, nblk, dt);
     return cudaGetLastError();
+}
+
+cudaError_t launch_first_dt(const MeshDev& m, int nblk, const double* U, double* dt, unsigned long long* lbmax,
+                            cudaStream_t st) {
+    if (!m.sub || !lbmax || (m.ndim != 2 && m.ndim != 3)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(lbmax, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)nblk, cell_chunks(m));
+    if (m.ndim == 3) {
+        first_dt_bounds_kernel<3><<<grid, 256, 0, st>>>(m, U, lbmax);
+        first_dt_eval_kernel<3><<<grid, 256, 0, st>>>(m, U, lbmax);
+    } else {
+        first_dt_bounds_kernel<2><<<grid, 256, 0, st>>>(m, U, lbmax);
+        first_dt_eval_kernel<2><<<grid, 256, 0, st>>>(m, U, lbmax);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dt_reduce_kernel<<<1, 1024, 0, st>>>(m, nblk, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemsetAsync(m.sub, 0, sizeof(unsigned long long) * (size_t)nblk, st);
 }
 
 }  // namespace orcha

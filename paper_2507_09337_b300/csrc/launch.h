@@ -106,6 +106,12 @@ cudaError_t launch_unpack_ids(const MeshDev& m, const int* ids, int n, const dou
                               cudaStream_t st);
 cudaError_t launch_signal_speed(const MeshDev& m, const int* ids, int n, const double* U, cudaStream_t st);
 cudaError_t launch_dt_reduce(const MeshDev& m, int nblk, double* dt, cudaStream_t st);
+// The first CFL time step of U with the signal-speed filter (kernels.cu): the
+// same dt bits as launch_signal_speed_all (FP64 rule) + launch_dt_reduce, with
+// FP64 speeds only where a cell can hold the maximum. Needs m.sub (nblk
+// entries) and m.smax zero on entry (left zero) and one scratch word lbmax.
+cudaError_t launch_first_dt(const MeshDev& m, int nblk, const double* U, double* dt, unsigned long long* lbmax,
+                            cudaStream_t st);
 // Signal speed of every block 0..nblk-1 (one CTA per block, no id list).
 // f32: the FP32-flux variant's signal-speed rule (its first dt), else FP64.
 cudaError_t launch_signal_speed_all(const MeshDev& m, int nblk, const double* U, cudaStream_t st,

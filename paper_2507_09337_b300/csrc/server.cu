@@ -249,9 +249,16 @@ bool orcha_server::admit(Req* r) {
         SRV_CUDA(orcha::launch_region_init(r->m, r->state[0], r->d.init_kind, reg, rs, copy), "admit recipe");
     }
     SRV_CUDA(cudaMemsetAsync(tail, 0, tail_bytes, copy), "admit clear");
-    SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy, orcha::prec_f32_dt(r->prec)),
-             "admit signal speed");
-    SRV_CUDA(orcha::launch_dt_reduce(r->m, (int)r->nblk, r->dt, copy), "admit dt");
+    if (orcha::prec_f32_dt(r->prec)) {
+        SRV_CUDA(orcha::launch_signal_speed_all(r->m, (int)r->nblk, r->state[0], copy, true), "admit signal speed");
+        SRV_CUDA(orcha::launch_dt_reduce(r->m, (int)r->nblk, r->dt, copy), "admit dt");
+    } else {
+        // FP64 speeds only where a cell can hold the maximum; the first word of
+        // the request's totals (written again when it completes) is the scratch
+        SRV_CUDA(orcha::launch_first_dt(r->m, (int)r->nblk, r->state[0], r->dt,
+                                        reinterpret_cast<unsigned long long*>(r->totals), copy),
+                 "admit dt");
+    }
     SRV_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming), "admit event");
     SRV_CUDA(cudaEventRecord(r->ev, copy), "admit record");
     r->st = RS::Admitting;

@@ -33,11 +33,12 @@ def _packet_steps(spec, U0, task, nsteps, dt0=None):
     mesh = B.Mesh(spec)
     try:
         mesh.load(U0)
+        dts = []
         if dt0 is None:
             mesh.advance(0, task, init_dt=True)
+            dts.append(mesh.dt_value())       # the first dt: every cell's speed in FP64
         else:
             mesh.dt.fill_(dt0)
-        dts = []
         for _ in range(nsteps):
             mesh.advance(1, task, init_dt=False)
             dts.append(mesh.dt_value())
@@ -56,12 +57,14 @@ def _batch_steps(spec, U0, task, nsteps, dt0=None, use_graph=False):
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         batch = B.orcha_batch_create(mesh.packets, 0, 0)
+        dts = []
         if dt0 is None:
             B.orcha_batch_advance(batch, task, 0, True, False, s)
+            s.synchronize()
+            dts.append(mesh.dt_value())       # the first dt: filtered for the FP64 rule
         else:
             mesh.dt.fill_(dt0)
             s.wait_stream(torch.cuda.current_stream())
-        dts = []
         for _ in range(nsteps):
             B.orcha_batch_advance(batch, task, 1, False, use_graph, s)
             s.synchronize()
@@ -75,7 +78,8 @@ def _batch_steps(spec, U0, task, nsteps, dt0=None, use_graph=False):
 
 def test_bound_is_an_upper_bound():
     """2^24 random states, heavy cancellation included: the FP32 bound never
-    lies below the FP64 speed, never applies to a state the FP64 path finds
+    lies below the FP64 speed (and the lower bound that the filtered first
+    time step pairs with it never above it), never applies to a state the FP64 path finds
     non-physical, and applies to about half of them (the rest lie outside
     its range or cancel to below 2^-40 E). Where the pressure is a
     near-cancellation the bound is loose (its FP32 interval for p is
@@ -133,6 +137,35 @@ def test_threshold_above_every_cell_falls_back(state):
     assert ea == 0 and eg == 0
     assert np.array_equal(da, dg)
     assert np.array_equal(A, G)
+
+
+@pytest.mark.parametrize("task", [B.ORCHA_TASK_HYDRO_FP64, B.ORCHA_TASK_HYDRO_FF])
+def test_first_dt_mixed_bounds_bitwise(task):
+    """The filtered first time step on a state whose cells take every branch:
+    fast cells whose pressure is below 2^-40 of their energy (no FP32 bounds:
+    evaluated in FP64 by the first pass), a two-state jump whose faster half
+    ties at the maximum (every cell of it evaluated), and a slow background
+    (skipped). The first dt and two steps equal the unfiltered packet path
+    bit for bit; with the fast cells (first dt only: their near-vacuum jet is
+    not meant to be stepped) the largest speed lies among the cells without
+    bounds, without them among the tied ones."""
+    spec = wl.MeshSpec(ndim=3, nb=(3, 2, 2), bs=(8, 8, 8))
+    for fast in (True, False):
+        U0 = wl.uniform_state(spec, 1.0, (0.0, 0.0, 0.0), 1.0)
+        U0[:6, 4] = 10.0 / 0.4                       # blocks 0..5: p = 10, the faster half
+        if fast:
+            rho, u, p = 1.0, 30.0, 1.0e-12           # p / E ~ 2e-15: no FP32 bounds
+            U0[7, :, 2:4, 3, 5] = 0.0
+            U0[7, 0, 2:4, 3, 5] = rho
+            U0[7, 2, 2:4, 3, 5] = rho * u
+            U0[7, 4, 2:4, 3, 5] = p / 0.4 + 0.5 * rho * u * u
+        n = 0 if fast else 2
+        A, da, ea = _packet_steps(spec, U0, task, n)
+        G, dg, eg = _batch_steps(spec, U0, task, n)
+        assert len(da) == n + 1
+        assert ea == 0 and eg == 0
+        assert np.array_equal(da, dg), (fast, da, dg)
+        assert np.array_equal(A, G)
 
 
 def test_2d_sod_bitwise():
