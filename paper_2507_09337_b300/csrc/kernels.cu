@@ -345,10 +345,21 @@ __global__ void block_totals_kernel(const MeshDev m, const double* __restrict__ 
     const int ncell = m.bs[0] * m.bs[1] * m.bs[2];
     {
         const int v = blockIdx.y;                    // one CTA per (block, variable)
-        double acc = 0.0;
+        // four independent partial sums per thread (cells c, c + 256, c + 512,
+        // c + 768 of each stride of 1024), added in a fixed order: the loads
+        // of a thread are in flight together instead of one after another
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         const double* Uv = U + (long long)blk * m.blk_stride + v * m.var_stride;
-        for (int c = threadIdx.x; c < ncell; c += blockDim.x) acc += Uv[cell_offset(m, c)];
-        red[threadIdx.x] = acc;
+        const int nb = blockDim.x;
+        int c = threadIdx.x;
+        for (; c + 3 * nb < ncell; c += 4 * nb) {
+            a0 += Uv[cell_offset(m, c)];
+            a1 += Uv[cell_offset(m, c + nb)];
+            a2 += Uv[cell_offset(m, c + 2 * nb)];
+            a3 += Uv[cell_offset(m, c + 3 * nb)];
+        }
+        for (; c < ncell; c += nb) a0 += Uv[cell_offset(m, c)];
+        red[threadIdx.x] = (a0 + a1) + (a2 + a3);
         __syncthreads();
         for (int o = 128; o > 0; o >>= 1) {
             if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
