@@ -308,8 +308,10 @@ ORCHA_API orcha_status orcha_batch_destroy(orcha_batch* batch);
 
 /* nsteps steps of every mesh in the batch on `stream` (hydro_task as for
  * orcha_mesh_advance; a HYDRO_RK2 step is two launches, one per stage).
- * init_dt != 0 first forms each mesh's dt from its current state
- * (signal-speed task + dt reduce); otherwise each mesh's dt_dev must already
+ * init_dt != 0 first forms each mesh's dt from its current state (the
+ * value of the signal-speed task + dt reduce; for the FP64 speed rule the
+ * FP64 speed is evaluated only where FP32 bounds leave a cell that can hold
+ * the maximum, with the same bits); otherwise each mesh's dt_dev must already
  * hold its time step. use_graph != 0 captures the nsteps steps' launches
  * once per (task, nsteps) and replays the graph (needs a non-default
  * stream). After the call each mesh's current buffer is the one its last
