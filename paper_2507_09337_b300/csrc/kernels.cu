@@ -53,10 +53,18 @@ __global__ void guard_fill_kernel(const MeshDev m, const int* __restrict__ blk_i
 // ---------------------------------------------------------------- pack / unpack
 // Interior array [block][var][k][j][i] <-> padded state interior. One CTA per
 // (block, var) plane; in-block cell indices are 32-bit (a block has at most
-// 32^3 cells), so no 64-bit division runs per cell.
+// 32^3 cells). Block sizes are 8, 16 or 32 (1 on an inactive axis; the mesh
+// descriptor is rejected otherwise), so the cell index splits by masks and
+// shifts instead of integer divisions.
+__device__ __forceinline__ void cell_ijk(const MeshDev& m, int c, int& i, int& j, int& k) {
+    const int r = c >> (__ffs(m.bs[0]) - 1);
+    i = c & (m.bs[0] - 1);
+    j = r & (m.bs[1] - 1);
+    k = r >> (__ffs(m.bs[1]) - 1);
+}
 __device__ __forceinline__ int cell_offset(const MeshDev& m, int c) {
-    const int i = c % m.bs[0], r = c / m.bs[0];
-    const int j = r % m.bs[1], k = r / m.bs[1];
+    int i, j, k;
+    cell_ijk(m, c, i, j, k);
     const int kk = (m.ndim == 3) ? k + kGuard : 0;
     return (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
 }
@@ -192,7 +200,8 @@ __device__ __forceinline__ bool speed_bounds(const SpeedBound& sb, const SpeedBo
 
 template <int NDIM>
 __device__ __forceinline__ void cell_state(const MeshDev& m, const double* __restrict__ Ub, int c, rd (&Un)[NDIM + 2]) {
-    const int i = c % m.bs[0], r0 = c / m.bs[0], j = r0 % m.bs[1], k = r0 / m.bs[1];
+    int i, j, k;
+    cell_ijk(m, c, i, j, k);
     const int kk = (NDIM == 3) ? k + kGuard : 0;
     const int po = (kk * m.pad[1] + (j + kGuard)) * m.pad[0] + (i + kGuard);
 #pragma unroll
@@ -315,7 +324,8 @@ __global__ void region_init_kernel(const MeshDev m, double* __restrict__ U, int 
     const int b[3] = {blk % m.nb[0], (blk / m.nb[0]) % m.nb[1], blk / (m.nb[0] * m.nb[1])};
     double* Ub = U + (long long)blk * m.blk_stride;
     for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncell; c += gridDim.y * blockDim.x) {
-        const int l[3] = {c % m.bs[0], (c / m.bs[0]) % m.bs[1], c / (m.bs[0] * m.bs[1])};
+        int l[3];
+        cell_ijk(m, c, l[0], l[1], l[2]);
         long long g[3];
         for (int d = 0; d < 3; ++d) g[d] = (long long)b[d] * m.bs[d] + l[d];
         bool in;
