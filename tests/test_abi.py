@@ -76,6 +76,10 @@ def test_state_elems_counts_padded_cells(L):
 @pytest.mark.parametrize("kw,msg", [
     (dict(ndim=4), "ndim"),
     (dict(bs=(12, 16, 16)), "bs[0]"),
+    # the kernels split a block's cell index by masks and shifts: only 8, 16 or 32
+    (dict(bs=(16, 24, 16)), "bs[1]"),
+    (dict(bs=(16, 16, 64)), "bs[2]"),
+    (dict(bs=(4, 16, 16)), "bs[0]"),
     (dict(ndim=2, nb=(2, 2, 2), bs=(8, 8, 1)), "2D"),
     (dict(gamma=1.0), "gamma"),
 ])
